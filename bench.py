@@ -1,0 +1,287 @@
+"""Benchmark: time-to-1e-9 relative residual of SLD-deflated Jacobi-PCG on the
+256x256x128 lognormal-layered point-source workload (8.4M cells, 4x4x4
+subdomains x 2 levelsets = 128 deflation vectors), one GB300.
+
+One step = one full solve (steps a4-a8 in one persistent launch: initial
+projection, deflated CG iterations, FP64 refinement, back-projection) from a
+right-hand side resident in HBM to the solution in HBM, followed by the FP64
+true-residual check.  The headline is the FP32-inner / FP64-refined form;
+plain FP64 is measured in the same run.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+With torchrun (N > 1) every rank solves its own replica (the path has no
+cross-GPU exchange at this size: "replicas only"); rank 0 prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-1e-9 rel. residual & HBM GB/s: mixed/learned/batched vs plain FP64"
+WORKLOAD = "lognormal-layered 256x256x128, point source, 4x4x4 subdomains x 2 levelsets (d=128), tol 1e-9"
+# algorithmic bytes per cell: one FP32 inner iteration (sweeps
+# A and B) and one FP64 refinement step (sweeps O1 and O2)
+BYTES_ITER_FP32 = 64
+BYTES_ITER_FP64 = 120 + 16  # + stored diagonal and inverse diagonal, read once per sweep
+BYTES_OUTER = 152
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_baseline(P, A=None, lab=None, iters_full=None, sample_iters=40, threads=None):
+    """Time the CPU oracle on a bounded sample: `sample_iters` deflated-CG
+    iterations (plus its setup), scaled to the full iteration count."""
+    import oracle
+    oracle.build()
+    if threads:
+        oracle.set_threads(threads)
+    t0 = time.perf_counter()
+    if A is None:
+        A = oracle.assemble(P.K, P.q, P.bc_type, P.bc_value)
+        lab = oracle.labels(P.K, P.S, P.tau, P.L)
+    t1 = time.perf_counter()
+    r = oracle.dpcg(A, lab, P.d, tol=P.tol, maxiter=sample_iters)
+    t2 = time.perf_counter()
+    # the sample includes the oracle's coarse setup; charge it once
+    per_iter = (t2 - t1) / max(1, r.iterations)
+    full = iters_full if iters_full else r.iterations
+    est_s = (t1 - t0) + per_iter * full
+    return {"value": est_s * 1e3, "unit": "ms", "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"oracle FP64 DPCG, {r.iterations} iterations of the full workload "
+                      f"({t2 - t1:.1f} s incl. coarse setup) + assembly/labels ({t1 - t0:.1f} s), "
+                      f"scaled to {full} iterations"}
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    from paper_1510_02148_gb300 import workloads as W
+    import oracle
+    P = W.lognormal_point_source()
+    A = oracle.assemble(P.K, P.q, P.bc_type, P.bc_value)
+    lab = oracle.labels(P.K, P.S, P.tau, P.L)
+    full_iters = int(os.environ.get("SLD_REF_FULL_ITERS", "0")) or None
+    vals = []
+    cb = None
+    for k in range(args.warmup + args.steps):
+        cb = cpu_baseline(P, A, lab, iters_full=full_iters, sample_iters=8)
+        if k >= args.warmup:
+            vals.append(cb["value"])
+    v = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": "FP64 oracle (CPU)"},
+            "cpu_baseline": {"kind": "oracle", "cores": cb["cores"], "sample": cb["sample"], "value": v,
+                             "unit": "ms"},
+            "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    from paper_1510_02148_gb300 import _build, sld, workloads as W
+
+    world, rank, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    _build.build()
+    sld.load()
+    stream = torch.cuda.current_stream()
+
+    P = W.lognormal_point_source(seed=1 + rank)
+    Kd = torch.from_numpy(P.K.reshape(-1)).cuda()
+    qd = torch.from_numpy(P.q.reshape(-1)).cuda()
+    t0 = time.perf_counter()
+    s = sld.System(Kd, qd, P.bc_type, P.bc_value, stream=stream.cuda_stream, shape=P.shape)
+    s.make_labels(P.S, P.tau, P.L)
+    s.build_deflation(P.d)
+    torch.cuda.synchronize()
+    setup_ms = (time.perf_counter() - t0) * 1e3
+    x = torch.empty(P.n, dtype=torch.float64, device="cuda")
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # --- plain FP64 (comparison) ---
+    fp64 = []
+    for _ in range(1 + args.fp64_steps):
+        _, info64 = s.solve(x=x, precision=sld.FP64)
+        fp64.append(info64)
+    fp64_ms = statistics.median(i.solve_ms for i in fp64[1:])
+    # --- mixed precision (headline) ---
+    for _ in range(args.warmup):
+        s.solve(x=x, precision=sld.FP32_IR)
+    infos = []
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            _, info = s.solve(x=x, precision=sld.FP32_IR)
+            infos.append(info)
+        ev1.record(stream)
+        barrier()
+    total_ms = ev0.elapsed_time(ev1)
+    ms_step = total_ms / args.steps
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    info = infos[-1]
+    kern_ms = statistics.median(i.solve_ms for i in infos)
+    n = P.n
+    alg_bytes = n * (BYTES_ITER_FP32 * info.iterations + BYTES_OUTER * info.outer_steps)
+    hbm_peak, peak_kind = _peaks()
+    achieved = alg_bytes / (kern_ms * 1e-3) / 1e9
+    alg64 = n * (BYTES_ITER_FP64 * fp64[-1].iterations + BYTES_OUTER * fp64[-1].outer_steps)
+    # --- end to end through the public API: host K, q in, host x out ---
+    Kh = torch.from_numpy(P.K.reshape(-1)).pin_memory()
+    qh = torch.from_numpy(P.q.reshape(-1)).pin_memory()
+    xh = torch.empty(P.n, dtype=torch.float64).pin_memory()
+    e2e = []
+    for k in range(2):
+        barrier()
+        t = time.perf_counter()
+        s2 = sld.System(Kh, qh, P.bc_type, P.bc_value, stream=stream.cuda_stream, shape=P.shape)
+        s2.make_labels(P.S, P.tau, P.L)
+        s2.build_deflation(P.d)
+        s2.solve(x=xh, precision=sld.FP32_IR)
+        barrier()
+        e2e.append((time.perf_counter() - t) * 1e3)
+        s2.close()
+    e2e_ms = min(e2e)
+
+    line = {
+        "metric": METRIC, "value": ms_step, "unit": "ms", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 inner / f64 refinement",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "d": P.d, "precision": "FP32_IR",
+                   "l2": "inputs larger than L2 (faces+vectors ~0.9 GB)", "parallelism": "replicas"},
+        "iterations": info.iterations, "outer_steps": info.outer_steps, "true_relres": info.true_relres,
+        "fp64": {"ms": fp64_ms, "iterations": fp64[-1].iterations, "true_relres": fp64[-1].true_relres,
+                 "alg_gbs": alg64 / (fp64_ms * 1e-3) / 1e9},
+        "speedup_vs_fp64": fp64_ms / kern_ms,
+        "hbm_gbs": achieved,
+        "setup_ms": setup_ms,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "traffic": None,
+                     "kernel": "k_solve<float,4,true> (persistent)", "peak_kind": peak_kind},
+        "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(Kh.numel() * 8 + qh.numel() * 8),
+                "d2h_bytes_per_step": int(xh.numel() * 8),
+                "what": "sld_build_system(host K, q) + make_labels + build_deflation + sld_solve -> host x"},
+        "gpu_launches": 3 * args.steps,
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(P, iters_full=fp64[-1].iterations, sample_iters=30)
+    s.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,198 @@
+/*
+ * sld.h -- C ABI of libsld: subdomain-levelset (SLD) deflated
+ * Jacobi-preconditioned CG for the cell-centred two-point-flux pressure matrix
+ * on a structured 3-D grid, on one GB300 GPU.
+ *
+ * Paper: J.H. van der Linden, T.B. Jonsthovel, A.A. Lukyanov, C. Vuik,
+ * "The parallel subdomain-levelset deflation method in reservoir simulation",
+ * arXiv:1510.02148.
+ *   - pressure equation -div(lambda grad p) = q ............ Section 2, eq. (pressure)
+ *   - linear system A x = b ................................ Section 2, eq. (coupledsys)
+ *   - E = Z^T A Z, P_1 = I - A Z E^{-1} Z^T, P_2 = I - Z E^{-1} Z^T A
+ *                                                     ...... Section 3.1, Def. 3.1, eqs. (E), (deflops)
+ *   - x = Z E^{-1} Z^T b + P_2 xhat with P_1 A xhat = P_1 b
+ *                                                     ...... Section 3.1, eqs. (defsplit), (defsys), (projectback)
+ *   - subdomain / levelset / subdomain-levelset vectors .... Section 3.2.2, eq. (domdefl)
+ *   - one subdomain per processor, vectors zero outside it . Section 3.2.2 (parallel SLD)
+ *
+ * Conventions
+ *   Grid: nx * ny * nz unit cells, cell (ix, iy, iz) has index
+ *         i = (iz * ny + iy) * nx + ix  (x fastest).  n = nx * ny * nz.
+ *   Pointers: every array argument may be host memory or device memory of the
+ *         handle's device; the library tells them apart with
+ *         cudaPointerGetAttributes.  Inputs are copied into buffers the handle
+ *         owns; outputs are written into the caller's memory.  Nothing is
+ *         returned that the caller frees, except the handle (sld_destroy).
+ *   Streams: all device work of a handle runs on the stream given to
+ *         sld_build_system (NULL = the legacy default stream).  Calls that
+ *         return data to host memory synchronise that stream.
+ *   Errors: every call returns an sld_status; sld_last_error() gives a
+ *         message (thread-local).  No call traps or asserts on the device;
+ *         every device-side wait is bounded and reports SLD_ERR_TIMEOUT.
+ *   Precision: the assembled operator, E, its factor and inverse, and the
+ *         refinement residual are FP64.  SLD_FP32_IR runs the inner deflated
+ *         iteration in FP32 (FP32 faces and vectors, FP64 coarse solve);
+ *         SLD_BF16COEF_IR stores the inner stencil coefficients in BF16 with
+ *         an FP32 per-cell inverse diagonal.
+ *   The GPU must be sm_103 (GB300); there is no CPU fallback.
+ */
+#ifndef SLD_H
+#define SLD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sld_system_s* sld_system; /* opaque; owns its device buffers */
+
+typedef enum {
+  SLD_OK = 0,
+  SLD_ERR_INVALID_ARG = 1,      /* bad size, pointer, label, K <= 0 or not finite */
+  SLD_ERR_CUDA = 2,             /* a CUDA runtime call failed (message has the CUDA error) */
+  SLD_ERR_NOT_CONVERGED = 3,    /* maxiter / max_outer reached; x holds the last iterate */
+  SLD_ERR_BREAKDOWN = 4,        /* p^T P A p <= 0 or a non-finite scalar in the iteration */
+  SLD_ERR_COARSE_SINGULAR = 5,  /* E = Z^T A Z not SPD (Cholesky pivot <= 0) */
+  SLD_ERR_TIMEOUT = 6,          /* a device-side wait ran out; the context stays usable */
+  SLD_ERR_OOM = 7,              /* device allocation failed */
+  SLD_ERR_STATE = 8             /* call out of order (e.g. solve before build_deflation) */
+} sld_status;
+
+/* Boundary faces, in this order: -x, +x, -y, +y, -z, +z. */
+enum { SLD_BC_NOFLOW = 0, SLD_BC_DIRICHLET = 1 };
+
+/* Inner precision of the solve. */
+enum { SLD_FP64 = 0, SLD_FP32_IR = 1, SLD_BF16COEF_IR = 2 };
+
+typedef struct {
+  int nx, ny, nz; /* cells per axis, each >= 1; unit cell size */
+} sld_grid;
+
+/*
+ * type[f] = SLD_BC_NOFLOW: no flux through box face f.
+ * type[f] = SLD_BC_DIRICHLET: the cells on box face f are fixed-value cells
+ *   holding value[f] (identity rows; their couplings move into b, so A stays
+ *   symmetric positive definite).  A cell on several Dirichlet faces takes
+ *   the value of the first one in the order above.
+ * At least one face must be Dirichlet for A to be nonsingular.
+ */
+typedef struct {
+  int type[6];
+  double value[6];
+} sld_bc;
+
+typedef struct {
+  int precision;          /* SLD_FP64 (default), SLD_FP32_IR, SLD_BF16COEF_IR */
+  double tol;             /* stop when ||b - A x||_2 <= tol * ||b||_2 (default 1e-9) */
+  double inner_tol;       /* mixed modes: residual reduction per inner solve (default 1e-5) */
+  int maxiter;            /* cap on iterations summed over inner solves (default 20000) */
+  int max_outer;          /* mixed modes: cap on refinement steps (default 40) */
+  int ctas_per_sm;        /* persistent-kernel CTAs per SM; 0 = as many as fit */
+  double timeout_s;       /* bound on every device-side wait, seconds (default 2.0) */
+  int debug_skip_barrier; /* test hook: CTA 0 skips the k-th barrier arrival of the
+                             solve so that the other CTAs' bounded waits run out
+                             (SLD_ERR_TIMEOUT); -1 = off (default) */
+} sld_options;
+
+typedef struct {
+  int iterations;          /* deflated-CG iterations (steps a4-a6), summed over inner solves */
+  int outer_steps;         /* refinement steps; 1 for SLD_FP64 */
+  double true_relres;      /* ||b - A x||_2 / ||b||_2, recomputed in FP64 after the solve */
+  double recursive_relres; /* the iteration's own deflated residual at exit, / ||b|| */
+  double solve_ms;         /* device time of the persistent solve kernel (CUDA events) */
+} sld_result;
+
+/* Fill *o with the defaults listed above. */
+void sld_default_options(sld_options* o);
+
+/*
+ * Assemble A and b for -div(K grad p) = q (Section 2, eq. (pressure) with
+ * the total mobility lambda := K, single phase).  Two-point flux: the
+ * transmissibility of the face between cells i and j is the harmonic mean
+ * (2 K_i K_j) / (K_i + K_j), evaluated in that order in FP64.
+ *   K: n values > 0 and finite.  q: n values or NULL (= 0).
+ *   stream: a cudaStream_t (NULL = default stream).
+ * On success *out is a new handle.  Errors: SLD_ERR_INVALID_ARG (sizes,
+ * K <= 0 or non-finite, no Dirichlet face), SLD_ERR_OOM, SLD_ERR_CUDA.
+ */
+sld_status sld_build_system(const double* K, const double* q, sld_grid g, sld_bc bc,
+                            void* stream, sld_system* out);
+
+/*
+ * Subdomain-levelset labels (Section 3.2.2, eq. (domdefl) per
+ * (subdomain, levelset) region; one set of vectors per subdomain as in the
+ * parallel form).  Subdomain of cell i: sx = floor(ix * Sx / nx) (likewise
+ * y, z), s = (sz * Sy + sy) * Sx + sx.  Levelset class: the number of
+ * thresholds tau[m] (m < L-1, ascending) with K_i >= tau[m].
+ * label_i = s * L + class_i, so d = Sx * Sy * Sz * L.
+ *   tau: L-1 values (host or device; may be NULL when L == 1).
+ *   labels_out: n int32 (host or device) or NULL.
+ * The labels stay on the device for sld_build_deflation(s, NULL, d, ...).
+ * Errors: SLD_ERR_INVALID_ARG (S < 1 or S > grid size, L < 1, d > 65535).
+ */
+sld_status sld_make_labels(sld_system s, int Sx, int Sy, int Sz, const double* tau, int L,
+                           int32_t* labels_out);
+
+/*
+ * Deflation space Z = [Z_lab, Z_extra] (Section 3.1, Def. 3.1): Z_lab has d
+ * indicator columns (column labels[i] is 1 in row i), Z_extra k dense columns.
+ * Builds E = Z^T A Z (eq. (E)) on the device, pins E_cc = 1 for an empty
+ * column c, factors E = L L^T (FP64 Cholesky) and forms E^{-1}.
+ *   labels: n int32 in [0, d), or NULL to use those of sld_make_labels.
+ *   d: 1 .. 65535.
+ *   Zextra, k, zextra_dtype: reserved for extra dense vectors; pass NULL, 0, 0.
+ * Errors: SLD_ERR_INVALID_ARG (label out of range), SLD_ERR_COARSE_SINGULAR
+ * (a pivot <= 0), SLD_ERR_TIMEOUT, SLD_ERR_CUDA.
+ */
+sld_status sld_build_deflation(sld_system s, const int32_t* labels, int d, const void* Zextra,
+                               int k, int zextra_dtype);
+
+/*
+ * Solve A x = b by SLD-deflated Jacobi-PCG (the CG form of the deflated
+ * solve of Section 3.1: iterate on P_1 A xhat = P_1 b, M = diag(A), then
+ * x = Z E^{-1} Z^T b + P_2 xhat, eq. (projectback)).  One cooperative
+ * persistent kernel runs every iteration; in the mixed modes an FP64
+ * refinement loop (residual, coarse correction, x update) wraps FP32 inner
+ * solves inside the same launch.
+ *   b: n values, or NULL for the assembled right-hand side.
+ *   o: options or NULL for the defaults.
+ *   x: n values (output).  res: may be NULL.
+ * Errors: SLD_ERR_STATE (no deflation built), SLD_ERR_NOT_CONVERGED (x and
+ * res still written), SLD_ERR_BREAKDOWN, SLD_ERR_TIMEOUT, SLD_ERR_CUDA.
+ */
+sld_status sld_solve(sld_system s, const double* b, const sld_options* o, double* x,
+                     sld_result* res);
+
+/* Release the handle and its device memory.  NULL is ignored. */
+void sld_destroy(sld_system s);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* sld_last_error(void);
+
+/* ---------------------------------------------------------------------- */
+/* Per-step access, for parity tests of the individual steps.             */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * Copy out the assembled FP64 operator: face transmissibilities Tx, Ty, Tz
+ * (face between cell i and its +x / +y / +z neighbour, stored at i; 0 on the
+ * box boundary; couplings to Dirichlet cells included), the diagonal A_ii and
+ * the right-hand side b.  Any pointer may be NULL.  n values each.
+ */
+sld_status sld_get_operator(sld_system s, double* Tx, double* Ty, double* Tz, double* diag,
+                            double* b);
+
+/* y = A x with the FP64 operator (n values each). */
+sld_status sld_apply_A(sld_system s, const double* x, double* y);
+
+/* out = Z^T v (d values; the segmented sum over labels), FP64. */
+sld_status sld_restrict(sld_system s, const double* v, double* out);
+
+/* Copy out E (d*d, row-major) and E^{-1} (d*d); either may be NULL. */
+sld_status sld_get_coarse(sld_system s, double* E, double* Einv);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SLD_H */

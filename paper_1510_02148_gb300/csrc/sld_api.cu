@@ -1,0 +1,405 @@
+// sld_api.cu -- the C ABI of libsld (declared in include/sld.h): handle
+// lifetime, argument checks, host/device pointer marshalling, and the calls
+// into the setup and solve launchers.  No arithmetic of the method runs here.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "sld_internal.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+sld_status fail(sld_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+sld_status cuda_fail(cudaError_t e, const char* where) {
+  g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? SLD_ERR_OOM : SLD_ERR_CUDA;
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+cudaMemcpyKind kind_in(const void* src) {
+  return is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+}
+cudaMemcpyKind kind_out(const void* dst) {
+  return is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+}
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count) {
+  return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * std::max<size_t>(count, 1));
+}
+
+void dfree(void* p) {
+  if (p) cudaFree(p);
+}
+
+__global__ void k_count_bad_K(int64_t n, const double* __restrict__ K, unsigned long long* bad) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const double k = K[i];
+    if (!(k > 0.0) || !isfinite(k)) atomicAdd(bad, 1ull);
+  }
+}
+
+sld_status ensure_workspace(sld_system s, bool need_fp32) {
+  const int64_t n = s->g.n;
+  cudaError_t e;
+  if (!s->x) {
+    if ((e = dalloc(&s->x, n)) != cudaSuccess) return cuda_fail(e, "alloc x");
+    if ((e = dalloc(&s->r64, n)) != cudaSuccess) return cuda_fail(e, "alloc r");
+    if ((e = dalloc(&s->bwork, n)) != cudaSuccess) return cuda_fail(e, "alloc b");
+    double* v[4];
+    for (int k = 0; k < 4; ++k)
+      if ((e = dalloc(&v[k], n)) != cudaSuccess) return cuda_fail(e, "alloc vectors");
+    s->z = v[0];
+    s->p0 = v[1];
+    s->p1 = v[2];
+    s->xh = v[3];
+    if ((e = dalloc(&s->out, 64)) != cudaSuccess) return cuda_fail(e, "alloc out");
+    if ((e = dalloc(&s->bar, 64)) != cudaSuccess) return cuda_fail(e, "alloc barrier");
+    if ((e = dalloc(&s->status, 16)) != cudaSuccess) return cuda_fail(e, "alloc status");
+  }
+  if (s->part_rows == 0 || !s->part) {
+    s->part_rows = s->nsm * 8;
+    const int pstride = (sld::kMaxD + sld::kPartScalars + 3) / 4 * 4;
+    if ((e = dalloc(&s->part, (size_t)s->part_rows * pstride)) != cudaSuccess) return cuda_fail(e, "alloc partials");
+    if ((e = dalloc(&s->s_glob, sld::kMaxD)) != cudaSuccess) return cuda_fail(e, "alloc s");
+    if ((e = dalloc(&s->y_glob, sld::kMaxD)) != cudaSuccess) return cuda_fail(e, "alloc y");
+  }
+  if (need_fp32 && !s->Tx32) {
+    if ((e = dalloc(&s->Tx32, n)) != cudaSuccess) return cuda_fail(e, "alloc Tx32");
+    if ((e = dalloc(&s->Ty32, n)) != cudaSuccess) return cuda_fail(e, "alloc Ty32");
+    if ((e = dalloc(&s->Tz32, n)) != cudaSuccess) return cuda_fail(e, "alloc Tz32");
+    if ((e = sld::launch_quantize_fp32(s)) != cudaSuccess) return cuda_fail(e, "fp32 coefficients");
+  }
+  return SLD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void sld_default_options(sld_options* o) {
+  if (!o) return;
+  o->precision = SLD_FP64;
+  o->tol = 1e-9;
+  o->inner_tol = 1e-5;
+  o->maxiter = 20000;
+  o->max_outer = 40;
+  o->ctas_per_sm = 0;
+  o->timeout_s = 2.0;
+  o->debug_skip_barrier = -1;
+}
+
+const char* sld_last_error(void) { return g_last_error.c_str(); }
+
+sld_status sld_build_system(const double* K, const double* q, sld_grid g, sld_bc bc, void* stream,
+                            sld_system* out) {
+  g_last_error.clear();
+  if (!out) return fail(SLD_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!K) return fail(SLD_ERR_INVALID_ARG, "K is NULL");
+  if (g.nx < 1 || g.ny < 1 || g.nz < 1) return fail(SLD_ERR_INVALID_ARG, "grid sizes must be >= 1");
+  const int64_t n = (int64_t)g.nx * g.ny * g.nz;
+  if (n > ((int64_t)1 << 31) - 1) return fail(SLD_ERR_INVALID_ARG, "more than 2^31-1 cells");
+  bool anyd = false;
+  for (int f = 0; f < 6; ++f) {
+    if (bc.type[f] != SLD_BC_NOFLOW && bc.type[f] != SLD_BC_DIRICHLET)
+      return fail(SLD_ERR_INVALID_ARG, "bc.type must be SLD_BC_NOFLOW or SLD_BC_DIRICHLET");
+    if (bc.type[f] == SLD_BC_DIRICHLET) {
+      anyd = true;
+      if (!std::isfinite(bc.value[f])) return fail(SLD_ERR_INVALID_ARG, "Dirichlet value not finite");
+    }
+  }
+  if (!anyd) return fail(SLD_ERR_INVALID_ARG, "at least one Dirichlet face is needed (A singular otherwise)");
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  cudaDeviceProp prop;
+  if ((e = cudaGetDeviceProperties(&prop, dev)) != cudaSuccess) return cuda_fail(e, "device properties");
+  if (prop.major != 10 || prop.minor != 3)
+    return fail(SLD_ERR_CUDA, "libsld is built for sm_103 (GB300) only; device is sm_" +
+                                  std::to_string(prop.major) + std::to_string(prop.minor));
+  if (!prop.cooperativeLaunch) return fail(SLD_ERR_CUDA, "device without cooperative launch");
+  sld_system s = new sld_system_s();
+  s->device = dev;
+  s->nsm = prop.multiProcessorCount;
+  s->stream = static_cast<cudaStream_t>(stream);
+  s->g.nx = g.nx;
+  s->g.ny = g.ny;
+  s->g.nz = g.nz;
+  s->g.nxy = (int64_t)g.nx * g.ny;
+  s->g.n = n;
+  for (int f = 0; f < 6; ++f) {
+    s->bc_type[f] = bc.type[f];
+    s->bc_value[f] = bc.value[f];
+  }
+  s->g.dlo_x = bc.type[0] == SLD_BC_DIRICHLET;
+  s->g.dhi_x = bc.type[1] == SLD_BC_DIRICHLET;
+  s->g.dlo_y = bc.type[2] == SLD_BC_DIRICHLET;
+  s->g.dhi_y = bc.type[3] == SLD_BC_DIRICHLET;
+  s->g.dlo_z = bc.type[4] == SLD_BC_DIRICHLET;
+  s->g.dhi_z = bc.type[5] == SLD_BC_DIRICHLET;
+  double* qd = nullptr;
+  unsigned long long* bad = nullptr;
+  unsigned long long hbad = 0;
+  sld_status st = SLD_OK;
+  do {
+    if ((e = dalloc(&s->K, n)) != cudaSuccess) { st = cuda_fail(e, "alloc K"); break; }
+    if ((e = dalloc(&s->Tx, n)) != cudaSuccess) { st = cuda_fail(e, "alloc Tx"); break; }
+    if ((e = dalloc(&s->Ty, n)) != cudaSuccess) { st = cuda_fail(e, "alloc Ty"); break; }
+    if ((e = dalloc(&s->Tz, n)) != cudaSuccess) { st = cuda_fail(e, "alloc Tz"); break; }
+    if ((e = dalloc(&s->diag, n)) != cudaSuccess) { st = cuda_fail(e, "alloc diag"); break; }
+    if ((e = dalloc(&s->invdiag, n)) != cudaSuccess) { st = cuda_fail(e, "alloc invdiag"); break; }
+    if ((e = dalloc(&s->b, n)) != cudaSuccess) { st = cuda_fail(e, "alloc b"); break; }
+    if ((e = cudaEventCreate(&s->ev0)) != cudaSuccess) { st = cuda_fail(e, "event"); break; }
+    if ((e = cudaEventCreate(&s->ev1)) != cudaSuccess) { st = cuda_fail(e, "event"); break; }
+    if ((e = cudaMemcpyAsync(s->K, K, sizeof(double) * n, kind_in(K), s->stream)) != cudaSuccess) {
+      st = cuda_fail(e, "copy K");
+      break;
+    }
+    if (q) {
+      if ((e = dalloc(&qd, n)) != cudaSuccess) { st = cuda_fail(e, "alloc q"); break; }
+      if ((e = cudaMemcpyAsync(qd, q, sizeof(double) * n, kind_in(q), s->stream)) != cudaSuccess) {
+        st = cuda_fail(e, "copy q");
+        break;
+      }
+    }
+    if ((e = dalloc(&bad, 1)) != cudaSuccess) { st = cuda_fail(e, "alloc"); break; }
+    cudaMemsetAsync(bad, 0, sizeof(*bad), s->stream);
+    k_count_bad_K<<<(unsigned)((n + 255) / 256), 256, 0, s->stream>>>(n, s->K, bad);
+    cudaMemcpyAsync(&hbad, bad, sizeof(hbad), cudaMemcpyDeviceToHost, s->stream);
+    if ((e = cudaStreamSynchronize(s->stream)) != cudaSuccess) { st = cuda_fail(e, "check K"); break; }
+    if (hbad) {
+      st = fail(SLD_ERR_INVALID_ARG, std::to_string(hbad) + " permeability values are <= 0 or not finite");
+      break;
+    }
+    if ((e = sld::launch_assemble(s, qd)) != cudaSuccess) { st = cuda_fail(e, "assemble"); break; }
+    if ((e = cudaStreamSynchronize(s->stream)) != cudaSuccess) { st = cuda_fail(e, "assemble"); break; }
+  } while (false);
+  dfree(qd);
+  dfree(bad);
+  if (st != SLD_OK) {
+    sld_destroy(s);
+    return st;
+  }
+  *out = s;
+  return SLD_OK;
+}
+
+sld_status sld_make_labels(sld_system s, int Sx, int Sy, int Sz, const double* tau, int L, int32_t* labels_out) {
+  g_last_error.clear();
+  if (!s) return fail(SLD_ERR_INVALID_ARG, "handle is NULL");
+  if (Sx < 1 || Sy < 1 || Sz < 1 || Sx > s->g.nx || Sy > s->g.ny || Sz > s->g.nz)
+    return fail(SLD_ERR_INVALID_ARG, "subdomain counts must be in [1, grid size]");
+  if (L < 1 || L > 16) return fail(SLD_ERR_INVALID_ARG, "L must be in [1, 16]");
+  if (L > 1 && !tau) return fail(SLD_ERR_INVALID_ARG, "tau is NULL");
+  const int64_t d = (int64_t)Sx * Sy * Sz * L;
+  if (d > sld::kMaxD) return fail(SLD_ERR_INVALID_ARG, "d = Sx*Sy*Sz*L exceeds " + std::to_string(sld::kMaxD));
+  double htau[16] = {0};
+  if (L > 1) {
+    cudaError_t e = cudaMemcpy(htau, tau, sizeof(double) * (L - 1), is_device_ptr(tau) ? cudaMemcpyDeviceToHost
+                                                                                         : cudaMemcpyHostToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "copy tau");
+    for (int m = 0; m < L - 1; ++m) {
+      if (!std::isfinite(htau[m])) return fail(SLD_ERR_INVALID_ARG, "tau not finite");
+      if (m > 0 && !(htau[m] > htau[m - 1])) return fail(SLD_ERR_INVALID_ARG, "tau must ascend strictly");
+    }
+  }
+  cudaError_t e;
+  if (!s->label && (e = dalloc(&s->label, s->g.n)) != cudaSuccess) return cuda_fail(e, "alloc labels");
+  if ((e = sld::launch_labels(s, Sx, Sy, Sz, htau, L)) != cudaSuccess) return cuda_fail(e, "labels");
+  s->have_labels_d = (int)d;
+  s->deflation_ready = false;
+  if (labels_out) {
+    if ((e = cudaMemcpyAsync(labels_out, s->label, sizeof(int32_t) * s->g.n, kind_out(labels_out), s->stream)) !=
+        cudaSuccess)
+      return cuda_fail(e, "copy labels out");
+  }
+  if ((e = cudaStreamSynchronize(s->stream)) != cudaSuccess) return cuda_fail(e, "labels");
+  return SLD_OK;
+}
+
+sld_status sld_build_deflation(sld_system s, const int32_t* labels, int d, const void* Zextra, int k,
+                               int zextra_dtype) {
+  g_last_error.clear();
+  (void)zextra_dtype;
+  if (!s) return fail(SLD_ERR_INVALID_ARG, "handle is NULL");
+  if (Zextra || k != 0) return fail(SLD_ERR_INVALID_ARG, "extra dense vectors are not supported by this entry point");
+  if (d < 1 || d > sld::kMaxD) return fail(SLD_ERR_INVALID_ARG, "d must be in [1, " + std::to_string(sld::kMaxD) + "]");
+  cudaError_t e;
+  if (labels) {
+    if (!s->label && (e = dalloc(&s->label, s->g.n)) != cudaSuccess) return cuda_fail(e, "alloc labels");
+    if ((e = cudaMemcpyAsync(s->label, labels, sizeof(int32_t) * s->g.n, kind_in(labels), s->stream)) != cudaSuccess)
+      return cuda_fail(e, "copy labels");
+  } else if (!s->label || s->have_labels_d == 0) {
+    return fail(SLD_ERR_STATE, "no labels: pass them or call sld_make_labels first");
+  }
+  if (d != s->d) {
+    dfree(s->E);
+    dfree(s->Einv);
+    s->E = s->Einv = nullptr;
+    if ((e = dalloc(&s->E, (size_t)d * d)) != cudaSuccess) return cuda_fail(e, "alloc E");
+    if ((e = dalloc(&s->Einv, (size_t)d * d)) != cudaSuccess) return cuda_fail(e, "alloc Einv");
+  }
+  s->d = d;
+  s->deflation_ready = false;
+  int bad = 0;
+  if ((e = sld::launch_coarse_E(s, &bad)) != cudaSuccess) return cuda_fail(e, "coarse matrix");
+  if (bad) return fail(SLD_ERR_INVALID_ARG, "a label is outside [0, d)");
+  std::string msg;
+  const int st = sld::coarse_factor(s, 2.0, &msg);
+  if (st != SLD_OK) return fail((sld_status)st, msg);
+  s->deflation_ready = true;
+  return SLD_OK;
+}
+
+sld_status sld_solve(sld_system s, const double* b, const sld_options* opt, double* x, sld_result* res) {
+  g_last_error.clear();
+  if (!s) return fail(SLD_ERR_INVALID_ARG, "handle is NULL");
+  if (!x) return fail(SLD_ERR_INVALID_ARG, "x is NULL");
+  if (!s->deflation_ready) return fail(SLD_ERR_STATE, "call sld_build_deflation before sld_solve");
+  sld_options o;
+  sld_default_options(&o);
+  if (opt) o = *opt;
+  if (o.precision != SLD_FP64 && o.precision != SLD_FP32_IR)
+    return fail(SLD_ERR_INVALID_ARG, "precision must be SLD_FP64 or SLD_FP32_IR");
+  if (!(o.tol > 0) || !(o.tol < 1)) return fail(SLD_ERR_INVALID_ARG, "tol must be in (0, 1)");
+  if (!(o.inner_tol > 0) || !(o.inner_tol < 1)) return fail(SLD_ERR_INVALID_ARG, "inner_tol must be in (0, 1)");
+  if (o.maxiter < 1 || o.max_outer < 1) return fail(SLD_ERR_INVALID_ARG, "maxiter and max_outer must be >= 1");
+  sld_status st = ensure_workspace(s, o.precision != SLD_FP64);
+  if (st != SLD_OK) return st;
+  const int64_t n = s->g.n;
+  const double* bd = s->b;
+  cudaError_t e;
+  if (b) {
+    if (is_device_ptr(b)) {
+      bd = b;
+    } else {
+      if ((e = cudaMemcpyAsync(s->bwork, b, sizeof(double) * n, cudaMemcpyHostToDevice, s->stream)) != cudaSuccess)
+        return cuda_fail(e, "copy b");
+      bd = s->bwork;
+    }
+  }
+  cudaMemsetAsync(s->status, 0, sizeof(int) * 4, s->stream);
+  sld_result r{};
+  std::string msg;
+  const int code = sld::run_solve(s, bd, o, &r, &msg);
+  if (code == SLD_ERR_CUDA || code == SLD_ERR_TIMEOUT || code < 0) {
+    if (res) *res = r;
+    return fail(code < 0 ? SLD_ERR_CUDA : (sld_status)code, msg);
+  }
+  double rr = 0, bb = 0;
+  if ((e = sld::launch_residual(s, bd, s->x, s->part, &rr, &bb)) != cudaSuccess) return cuda_fail(e, "residual");
+  r.true_relres = bb > 0 ? std::sqrt(rr / bb) : 0.0;
+  if ((e = cudaMemcpyAsync(x, s->x, sizeof(double) * n, kind_out(x), s->stream)) != cudaSuccess)
+    return cuda_fail(e, "copy x out");
+  if ((e = cudaStreamSynchronize(s->stream)) != cudaSuccess) return cuda_fail(e, "copy x out");
+  if (res) *res = r;
+  if (code != SLD_OK) return fail((sld_status)code, msg);
+  return SLD_OK;
+}
+
+void sld_destroy(sld_system s) {
+  if (!s) return;
+  if (s->stream) cudaStreamSynchronize(s->stream);
+  void* ptrs[] = {s->K, s->Tx, s->Ty, s->Tz, s->diag, s->invdiag, s->b, s->Tx32, s->Ty32, s->Tz32,
+                  s->label, s->E, s->Einv, s->x, s->r64, s->bwork, s->z, s->p0, s->p1, s->xh,
+                  s->part, s->s_glob, s->y_glob, s->out, s->bar, s->status};
+  for (void* p : ptrs) dfree(p);
+  if (s->ev0) cudaEventDestroy(s->ev0);
+  if (s->ev1) cudaEventDestroy(s->ev1);
+  delete s;
+}
+
+sld_status sld_get_operator(sld_system s, double* Tx, double* Ty, double* Tz, double* diag, double* b) {
+  g_last_error.clear();
+  if (!s) return fail(SLD_ERR_INVALID_ARG, "handle is NULL");
+  const size_t bytes = sizeof(double) * s->g.n;
+  const double* src[5] = {s->Tx, s->Ty, s->Tz, s->diag, s->b};
+  double* dst[5] = {Tx, Ty, Tz, diag, b};
+  for (int k = 0; k < 5; ++k) {
+    if (!dst[k]) continue;
+    cudaError_t e = cudaMemcpyAsync(dst[k], src[k], bytes, kind_out(dst[k]), s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "copy operator");
+  }
+  cudaError_t e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "copy operator");
+  return SLD_OK;
+}
+
+sld_status sld_apply_A(sld_system s, const double* x, double* y) {
+  g_last_error.clear();
+  if (!s || !x || !y) return fail(SLD_ERR_INVALID_ARG, "NULL argument");
+  const int64_t n = s->g.n;
+  double *xd = nullptr, *yd = nullptr;
+  cudaError_t e;
+  if ((e = dalloc(&xd, n)) != cudaSuccess) return cuda_fail(e, "alloc");
+  if ((e = dalloc(&yd, n)) != cudaSuccess) {
+    dfree(xd);
+    return cuda_fail(e, "alloc");
+  }
+  cudaMemcpyAsync(xd, x, sizeof(double) * n, kind_in(x), s->stream);
+  e = sld::launch_apply_A(s, xd, yd);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(y, yd, sizeof(double) * n, kind_out(y), s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  dfree(xd);
+  dfree(yd);
+  if (e != cudaSuccess) return cuda_fail(e, "apply A");
+  return SLD_OK;
+}
+
+sld_status sld_restrict(sld_system s, const double* v, double* out) {
+  g_last_error.clear();
+  if (!s || !v || !out) return fail(SLD_ERR_INVALID_ARG, "NULL argument");
+  if (!s->label || s->d < 1) return fail(SLD_ERR_STATE, "no deflation built");
+  const int64_t n = s->g.n;
+  double *vd = nullptr, *od = nullptr;
+  cudaError_t e;
+  if ((e = dalloc(&vd, n)) != cudaSuccess) return cuda_fail(e, "alloc");
+  if ((e = dalloc(&od, s->d)) != cudaSuccess) {
+    dfree(vd);
+    return cuda_fail(e, "alloc");
+  }
+  cudaMemcpyAsync(vd, v, sizeof(double) * n, kind_in(v), s->stream);
+  e = sld::launch_restrict(s, vd, od);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, od, sizeof(double) * s->d, kind_out(out), s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  dfree(vd);
+  dfree(od);
+  if (e != cudaSuccess) return cuda_fail(e, "restrict");
+  return SLD_OK;
+}
+
+sld_status sld_get_coarse(sld_system s, double* E, double* Einv) {
+  g_last_error.clear();
+  if (!s) return fail(SLD_ERR_INVALID_ARG, "handle is NULL");
+  if (!s->E) return fail(SLD_ERR_STATE, "no deflation built");
+  const size_t bytes = sizeof(double) * s->d * s->d;
+  cudaError_t e = cudaSuccess;
+  if (E) e = cudaMemcpyAsync(E, s->E, bytes, kind_out(E), s->stream);
+  if (e == cudaSuccess && Einv) e = cudaMemcpyAsync(Einv, s->Einv, bytes, kind_out(Einv), s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "copy coarse");
+  return SLD_OK;
+}
+
+}  // extern "C"

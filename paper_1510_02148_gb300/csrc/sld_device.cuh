@@ -1,0 +1,133 @@
+// sld_device.cuh -- device helpers shared by the libsld kernels:
+// bounded grid barrier, vector loads of four cells, warp reductions,
+// cell geometry and Dirichlet tests.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sld_internal.h"
+
+namespace sld {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ int ld_volatile_i32(const int* p) {
+  return *reinterpret_cast<const volatile int*>(p);
+}
+
+// Grid-wide barrier for a cooperative launch (all CTAs co-resident).
+// A monotone arrival counter: barrier number e completes when the counter
+// reaches e * gridDim.x.  Every wait is bounded by sy.timeout_ns; on expiry
+// the CTA records SLD_ERR_TIMEOUT in *sy.status and the barrier returns
+// false, as it does when another CTA has already recorded an error.  The
+// caller then leaves the kernel.  No trap, no unbounded spin.
+__device__ __forceinline__ bool grid_barrier(const SyncArgs& sy, unsigned& epoch) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ++epoch;
+    const unsigned target = epoch * gridDim.x;
+    const bool skip = sy.skip_epoch > 0 && blockIdx.x == 0 && epoch == (unsigned)sy.skip_epoch;
+    __threadfence();
+    if (!skip) atomicAdd(sy.count, 1u);
+    int ok = 1;
+    const unsigned long long t0 = global_ns();
+    unsigned spins = 0;
+    while (ld_acquire_u32(sy.count) < target) {
+      if (((++spins) & 63u) == 0) {
+        if (ld_volatile_i32(sy.status) != 0) { ok = 0; break; }
+        if (global_ns() - t0 > sy.timeout_ns) {
+          atomicCAS(sy.status, 0, (int)SLD_ERR_TIMEOUT);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+    if (ok && ld_volatile_i32(sy.status) != 0) ok = 0;
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// ---------------------------------------------------------------------------
+// Loads / stores of CX consecutive cells.  With CX == 4 and all four cells in
+// range the access is one 16-byte vector (float) or two (double); otherwise
+// element-wise with the missing cells read as 0.  `ro` selects the read-only
+// (non-coherent) path and must only be used for data the kernel never writes.
+// ---------------------------------------------------------------------------
+template <typename T, int CX, bool RO>
+__device__ __forceinline__ void ld_cells(const T* __restrict__ a, int64_t i, int nval, T (&v)[CX]) {
+  if constexpr (CX == 4) {
+    if (nval == 4) {
+      if constexpr (sizeof(T) == 4) {
+        float4 q = RO ? __ldg(reinterpret_cast<const float4*>(a + i)) : *reinterpret_cast<const float4*>(a + i);
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+      } else {
+        double2 q0 = RO ? __ldg(reinterpret_cast<const double2*>(a + i)) : *reinterpret_cast<const double2*>(a + i);
+        double2 q1 = RO ? __ldg(reinterpret_cast<const double2*>(a + i) + 1) : *(reinterpret_cast<const double2*>(a + i) + 1);
+        v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
+      }
+      return;
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < CX; ++c) v[c] = (c < nval) ? (RO ? __ldg(a + i + c) : a[i + c]) : T(0);
+}
+
+template <int CX>
+__device__ __forceinline__ void ld_labels(const int32_t* __restrict__ a, int64_t i, int nval, int (&v)[CX]) {
+  if constexpr (CX == 4) {
+    if (nval == 4) {
+      int4 q = __ldg(reinterpret_cast<const int4*>(a + i));
+      v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+      return;
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < CX; ++c) v[c] = (c < nval) ? __ldg(a + i + c) : -1;
+}
+
+template <typename T, int CX>
+__device__ __forceinline__ void st_cells(T* __restrict__ a, int64_t i, int nval, const T (&v)[CX]) {
+  if constexpr (CX == 4) {
+    if (nval == 4) {
+      if constexpr (sizeof(T) == 4) {
+        *reinterpret_cast<float4*>(a + i) = make_float4(v[0], v[1], v[2], v[3]);
+      } else {
+        reinterpret_cast<double2*>(a + i)[0] = make_double2(v[0], v[1]);
+        reinterpret_cast<double2*>(a + i)[1] = make_double2(v[2], v[3]);
+      }
+      return;
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < CX; ++c)
+    if (c < nval) a[i + c] = v[c];
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+// Dirichlet-cell test along one axis: coordinate c on a Dirichlet face.
+__device__ __forceinline__ bool dir_axis(int c, int n, unsigned lo, unsigned hi) {
+  return (lo && c == 0) || (hi && c == n - 1);
+}
+
+}  // namespace sld

@@ -1,0 +1,111 @@
+// sld_internal.h -- internal types of libsld: the handle, launch arguments,
+// and the launchers each translation unit provides.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/sld.h"
+
+namespace sld {
+
+// Tile of the persistent sweeps: each warp owns one grid row of TX cells
+// (32 lanes x CX cells), a CTA owns TY consecutive rows plus two halo rows
+// (one warp each) and marches through a range of z planes.
+constexpr int kTY = 8;                  // rows per tile
+constexpr int kWarps = kTY + 2;         // + two halo-row warps
+constexpr int kThreads = kWarps * 32;   // 320
+constexpr int kMaxD = 4096;             // largest d (labels) the kernels take
+constexpr int kWarpAccMaxD = 256;       // per-warp label accumulators up to this d
+constexpr int kPartScalars = 8;         // scalar slots after the d label sums
+
+struct SyncArgs {
+  unsigned* count;                // arrival counter, zeroed before the launch
+  int* status;                    // 0 or an sld_status, written on error
+  unsigned long long timeout_ns;  // bound on every wait
+  int skip_epoch;                 // test hook: CTA 0 does not arrive at this barrier (0 = off)
+};
+
+struct Geo {
+  int nx, ny, nz;
+  int64_t nxy, n;
+  unsigned dlo_x, dhi_x, dlo_y, dhi_y, dlo_z, dhi_z;  // Dirichlet faces
+};
+
+// Everything the persistent solve kernel reads and writes.
+struct SolveArgs {
+  Geo g;
+  int cx;                 // cells per lane in x (1 or 4)
+  int ntx, nty;           // column tiles in x and y
+  int64_t ntiles;         // ntx * nty * nz plane-tiles
+  int d;
+  const int32_t* label;
+  const double* Einv;     // d x d
+  // FP64 operator
+  const double *Tx64, *Ty64, *Tz64, *diag64, *invdiag64, *b;
+  double* x;              // solution (FP64)
+  double* r64;            // FP64 refinement residual
+  // inner operator and state, element type per mode (double or float)
+  const void *Txi, *Tyi, *Tzi;
+  void *z, *p0, *p1, *xh;
+  // reductions
+  double* part;           // [grid][pstride]
+  int pstride;
+  double* s_glob;         // d
+  double* y_glob;         // d
+  double* out;            // results: see kOut*
+  SyncArgs sy;
+  double tol, inner_tol;
+  int maxiter, max_outer;
+  int fp64;               // 1: inner in FP64, single inner solve + finalisation
+};
+
+enum {
+  kOutIters = 0, kOutOuter, kOutRR, kOutBB, kOutStatus, kOutRecRR, kOutCount = 8
+};
+
+}  // namespace sld
+
+struct sld_system_s {
+  int device = 0, nsm = 0;
+  cudaStream_t stream = nullptr;
+  sld::Geo g{};
+  int bc_type[6]{};
+  double bc_value[6]{};
+  // FP64 operator (assembled) and the permeability
+  double *K = nullptr, *Tx = nullptr, *Ty = nullptr, *Tz = nullptr;
+  double *diag = nullptr, *invdiag = nullptr, *b = nullptr;
+  // FP32 inner operator (lazily made)
+  float *Tx32 = nullptr, *Ty32 = nullptr, *Tz32 = nullptr;
+  // deflation
+  int32_t* label = nullptr;
+  int d = 0, have_labels_d = 0;
+  double *E = nullptr, *Einv = nullptr;
+  bool deflation_ready = false;
+  // solve work space (lazily made)
+  double *x = nullptr, *r64 = nullptr, *bwork = nullptr;
+  void *z = nullptr, *p0 = nullptr, *p1 = nullptr, *xh = nullptr;  // sized for FP64
+  double *part = nullptr, *s_glob = nullptr, *y_glob = nullptr, *out = nullptr;
+  unsigned* bar = nullptr;
+  int* status = nullptr;
+  int part_rows = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace sld {
+// sld_setup.cu
+cudaError_t launch_assemble(sld_system s, const double* q);
+cudaError_t launch_labels(sld_system s, int Sx, int Sy, int Sz, const double* tau, int L);
+cudaError_t launch_coarse_E(sld_system s, int* bad_label);
+int coarse_factor(sld_system s, double timeout_s, std::string* msg);  // returns sld_status
+cudaError_t launch_quantize_fp32(sld_system s);
+cudaError_t launch_apply_A(sld_system s, const double* x, double* y);
+cudaError_t launch_restrict(sld_system s, const double* v, double* out);
+cudaError_t launch_residual(sld_system s, const double* b, const double* x, double* partial_out,
+                            double* rr_host, double* bb_host);
+// sld_solve.cu
+int run_solve(sld_system s, const double* b_dev, const sld_options& o, sld_result* res,
+              std::string* msg);  // returns sld_status
+}  // namespace sld

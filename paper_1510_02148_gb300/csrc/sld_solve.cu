@@ -1,0 +1,925 @@
+// sld_solve.cu -- the persistent SLD-deflated Jacobi-PCG solve (steps a4-a8).
+//
+// One cooperative launch runs the whole solve.  Each CTA owns a fixed range
+// of "plane tiles" (a TX x 8 patch of one z plane); the ranges are contiguous
+// in (column tile, z), so a CTA marches up a column of the grid, keeping the
+// z-1, z, z+1 values of its rows in registers, exchanging the y neighbours
+// through shared memory and the x neighbours through warp shuffles.
+//
+// Per deflated-CG iteration (the CG form of the deflated solve of
+// Section 3.1, Def. 3.1: iterate on P A xhat = P b with P = I - A Z E^{-1} Z^T,
+// M = diag A):
+//   sweep A : p = z + beta p (also at halo cells), v = A p,
+//             s = Z^T v (segmented sum over labels), gamma = p.v
+//   barrier, s reduced column-wise; barrier, y = E^{-1} s row-wise; barrier
+//   every CTA: delta = p.P A p = gamma - s.y (A symmetric), alpha = rho/delta
+//   sweep B : u = p - Z y, w = A u (= P A p), xhat += alpha p,
+//             r = diag z - alpha w, z = r / diag, rho' = r.z, rr = r.r
+//   barrier, every CTA reduces rho', rr in the same order and takes the same
+//   branch.  The residual r is kept as z = M^{-1} r; r = diag * z.
+//
+// Refinement step (FP64, once per inner solve; also the initial projection
+// and the final back-projection, eq. (projectback)):
+//   O1: r' = b - A (x + xhat), s = Z^T r'
+//   barrier, reduce, barrier, y = E^{-1} s, barrier
+//   O2: x += xhat + Z y, rhat = r' - A Z y (= P r'), z = M^{-1} rhat, xhat = p = 0
+// With x = 0 this is x = Z E^{-1} Z^T b and rhat_0 = P b; after an inner solve
+// it is x = x + xhat + Z E^{-1} Z^T (b - A (x + xhat)), i.e. x* + P^T xhat.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "sld_device.cuh"
+#include "sld_internal.h"
+
+namespace sld {
+namespace {
+
+template <typename T, int CX, bool WACC>
+struct Cfg {
+  static constexpr int TX = 32 * CX;
+  static constexpr int HOFF = (CX == 4) ? int(16 / sizeof(T)) : 1;
+  static constexpr int RS = TX + 2 * HOFF;  // shared row stride (with x halo)
+};
+
+template <typename T>
+struct Sm {
+  T* P;        // [2][kTY+2][RS]   published neighbour values
+  T* Ty;       // [2][kTY+1][TX]   Ty of rows y0-1 .. y0+kTY-1
+  T* Txh;      // [2][kTY]         Tx of the face left of the tile
+  double* acc; // [kWarps][d] or [d]  label sums
+  double* Yd;  // [d] coarse correction, FP64
+  T* Y;        // [d] coarse correction, inner precision
+  double* red; // [64] block reduction scratch
+};
+
+template <typename T, int CX, bool WACC>
+__host__ __device__ constexpr size_t smem_bytes(int d) {
+  using C = Cfg<T, CX, WACC>;
+  size_t b = 0;
+  b += sizeof(T) * 2 * (kTY + 2) * C::RS;
+  b += sizeof(T) * 2 * (kTY + 1) * C::TX;
+  b += sizeof(T) * 2 * kTY;
+  b = (b + 15) / 16 * 16;
+  b += sizeof(double) * (size_t)(WACC ? kWarps : 1) * d;
+  b += sizeof(double) * d;
+  b += sizeof(T) * d;
+  b = (b + 15) / 16 * 16;
+  b += sizeof(double) * 64;
+  return b;
+}
+
+template <typename T, int CX, bool WACC>
+__device__ Sm<T> carve(unsigned char* base, int d) {
+  using C = Cfg<T, CX, WACC>;
+  Sm<T> s;
+  size_t o = 0;
+  s.P = reinterpret_cast<T*>(base + o);
+  o += sizeof(T) * 2 * (kTY + 2) * C::RS;
+  s.Ty = reinterpret_cast<T*>(base + o);
+  o += sizeof(T) * 2 * (kTY + 1) * C::TX;
+  s.Txh = reinterpret_cast<T*>(base + o);
+  o += sizeof(T) * 2 * kTY;
+  o = (o + 15) / 16 * 16;
+  s.acc = reinterpret_cast<double*>(base + o);
+  o += sizeof(double) * (size_t)(WACC ? kWarps : 1) * d;
+  s.Yd = reinterpret_cast<double*>(base + o);
+  o += sizeof(double) * d;
+  s.Y = reinterpret_cast<T*>(base + o);
+  o += sizeof(T) * d;
+  o = (o + 15) / 16 * 16;
+  s.red = reinterpret_cast<double*>(base + o);
+  return s;
+}
+
+// Reads of CX consecutive T from shared memory (16-byte aligned when CX == 4).
+template <typename T, int CX>
+__device__ __forceinline__ void sm_ld(const T* p, T (&v)[CX]) {
+  if constexpr (CX == 4) {
+    if constexpr (sizeof(T) == 4) {
+      float4 q = *reinterpret_cast<const float4*>(p);
+      v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    } else {
+      double2 q0 = reinterpret_cast<const double2*>(p)[0], q1 = reinterpret_cast<const double2*>(p)[1];
+      v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < CX; ++c) v[c] = p[c];
+  }
+}
+template <typename T, int CX>
+__device__ __forceinline__ void sm_st(T* p, const T (&v)[CX]) {
+  if constexpr (CX == 4) {
+    if constexpr (sizeof(T) == 4) {
+      *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+      reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+      reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < CX; ++c) p[c] = v[c];
+  }
+}
+
+// Block-wide sum of one double per thread (fixed order); result to all threads.
+__device__ double block_sum(double v, double* red) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  v = warp_sum(v);
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+  return t;
+}
+
+// Flush the per-lane run sums of a warp into the shared label accumulators.
+// Lanes are grouped by label; each group is summed in lane order and added
+// once by its lowest lane, so no two lanes of a warp write the same slot.
+template <bool WACC>
+__device__ __forceinline__ void warp_flush(int cur, double acc, double* sacc, int d, int warp) {
+  const int lane = threadIdx.x & 31;
+  const unsigned grp = __match_any_sync(kFull, cur);
+  double sum = 0.0;
+#pragma unroll 4
+  for (int src = 0; src < 32; ++src) {
+    const double v = __shfl_sync(kFull, acc, src);
+    if ((grp >> src) & 1u) sum += v;
+  }
+  if (cur >= 0 && lane == __ffs(grp) - 1) {
+    if constexpr (WACC) sacc[warp * d + cur] += sum;
+    else atomicAdd(&sacc[cur], sum);
+  }
+}
+
+// Where this thread sits for a segment (column tile, z range).
+struct Seg {
+  int x0, y0, z0, z1;
+  int y;      // the grid row this warp handles
+  bool own;   // an interior row (else a halo row)
+  int xl;     // first cell of this lane
+  int nv;     // valid cells of this lane (0 if the row is outside the grid)
+  int64_t rowbase;
+};
+
+template <int TX>
+__device__ __forceinline__ Seg make_seg(const SolveArgs& a, int64_t ct, int z0, int z1, int cx) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  Seg s;
+  const int tx = (int)(ct % a.ntx), ty = (int)(ct / a.ntx);
+  s.x0 = tx * TX;
+  s.y0 = ty * kTY;
+  s.z0 = z0;
+  s.z1 = z1;
+  s.own = warp < kTY;
+  s.y = s.own ? s.y0 + warp : (warp == kTY ? s.y0 - 1 : s.y0 + kTY);
+  s.xl = s.x0 + lane * cx;
+  const bool rowok = s.y >= 0 && s.y < a.g.ny;
+  s.nv = rowok ? max(0, min(cx, a.g.nx - s.xl)) : 0;
+  s.rowbase = (int64_t)s.y * a.g.nx + s.xl;
+  return s;
+}
+
+// The 7-point operator at one free or Dirichlet cell.
+//   FP32 inner form: sum over faces T (u_i - m_j u_j)  (m_j = 0 for a Dirichlet
+//   neighbour), exact zero row sums, no cancellation of diag * u against the
+//   neighbour sum.  FP64 form: diag u_i - sum m_j T u_j with the stored diagonal.
+template <typename T>
+__device__ __forceinline__ T stencil(bool dirc, T u, T dg, T fxm, T xm, bool mxm, T fxp, T xp, bool mxp, T fym,
+                                     T ym, bool mym, T fyp, T yp, bool myp, T fzm, T zm, bool mzm, T fzp, T zp,
+                                     bool mzp) {
+  if (dirc) return u;
+  if constexpr (sizeof(T) == 8) {
+    T s = dg * u;
+    s -= fxm * (mxm ? xm : T(0));
+    s -= fxp * (mxp ? xp : T(0));
+    s -= fym * (mym ? ym : T(0));
+    s -= fyp * (myp ? yp : T(0));
+    s -= fzm * (mzm ? zm : T(0));
+    s -= fzp * (mzp ? zp : T(0));
+    return s;
+  } else {
+    T s = fxm * (u - (mxm ? xm : T(0)));
+    s += fxp * (u - (mxp ? xp : T(0)));
+    s += fym * (u - (mym ? ym : T(0)));
+    s += fyp * (u - (myp ? yp : T(0)));
+    s += fzm * (u - (mzm ? zm : T(0)));
+    s += fzp * (u - (mzp ? zp : T(0)));
+    return s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Sweep A: p = z + beta p_old, v = A p, s = Z^T v, gamma = p . v
+// ---------------------------------------------------------------------------
+template <typename T, int CX, bool WACC>
+__device__ void sweep_A(const SolveArgs& a, const Sm<T>& sm, const T* zb, const T* pold, T* pnew, T beta,
+                        const T* __restrict__ Fx, const T* __restrict__ Fy, const T* __restrict__ Fz,
+                        double* part_row) {
+  using C = Cfg<T, CX, WACC>;
+  constexpr int TX = C::TX, RS = C::RS, HOFF = C::HOFF;
+  const Geo& g = a.g;
+  const int d = a.d;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int k = threadIdx.x; k < (WACC ? kTY : 1) * d; k += blockDim.x) sm.acc[k] = 0.0;
+  __syncthreads();
+  int cur = -1;
+  T run = T(0);
+  double dgam = 0.0;
+  const int64_t t0 = a.ntiles * blockIdx.x / gridDim.x, t1 = a.ntiles * (blockIdx.x + 1) / gridDim.x;
+  for (int64_t t = t0; t < t1;) {
+    const int64_t ct = t / g.nz;
+    const int z0 = (int)(t % g.nz);
+    const int z1 = (int)((int64_t)g.nz < (int64_t)z0 + (t1 - t) ? (int64_t)g.nz : (int64_t)z0 + (t1 - t));
+    t += z1 - z0;
+    const Seg sg = make_seg<TX>(a, ct, z0, z1, CX);
+    // p_new at this lane's cells of plane zz (0 outside the grid)
+    auto pnew_at = [&](int zz, T(&o)[CX]) {
+      if (zz < 0 || zz >= g.nz || sg.nv == 0) {
+#pragma unroll
+        for (int c = 0; c < CX; ++c) o[c] = T(0);
+        return;
+      }
+      T zv[CX], po[CX];
+      const int64_t i = (int64_t)zz * g.nxy + sg.rowbase;
+      ld_cells<T, CX, false>(zb, i, sg.nv, zv);
+      ld_cells<T, CX, false>(pold, i, sg.nv, po);
+#pragma unroll
+      for (int c = 0; c < CX; ++c) o[c] = zv[c] + beta * po[c];
+    };
+    auto pnew_scalar = [&](int x, int zz) -> T {
+      const int64_t i = (int64_t)zz * g.nxy + (int64_t)sg.y * g.nx + x;
+      return zb[i] + beta * pold[i];
+    };
+    T pm[CX], pc[CX], pn[CX], tzm[CX];
+    bool dxc[CX], dxm[CX], dxp[CX];
+#pragma unroll
+    for (int c = 0; c < CX; ++c) {
+      const int x = sg.xl + c;
+      dxc[c] = dir_axis(x, g.nx, g.dlo_x, g.dhi_x);
+      dxm[c] = dir_axis(x - 1, g.nx, g.dlo_x, g.dhi_x);
+      dxp[c] = dir_axis(x + 1, g.nx, g.dlo_x, g.dhi_x);
+    }
+    const bool dyc = dir_axis(sg.y, g.ny, g.dlo_y, g.dhi_y);
+    const bool dym = dir_axis(sg.y - 1, g.ny, g.dlo_y, g.dhi_y);
+    const bool dyp = dir_axis(sg.y + 1, g.ny, g.dlo_y, g.dhi_y);
+    if (sg.own) {
+      pnew_at(z0 - 1, pm);
+      pnew_at(z0, pc);
+      if (z0 > 0 && sg.nv > 0) ld_cells<T, CX, true>(Fz, (int64_t)(z0 - 1) * g.nxy + sg.rowbase, sg.nv, tzm);
+      else {
+#pragma unroll
+        for (int c = 0; c < CX; ++c) tzm[c] = T(0);
+      }
+    }
+    T gam = T(0);
+    for (int z = z0; z < z1; ++z) {
+      const int buf = z & 1;
+      T* sP = sm.P + buf * (kTY + 2) * RS;
+      T* sTy = sm.Ty + buf * (kTY + 1) * TX;
+      T* sTxh = sm.Txh + buf * kTY;
+      const int64_t iz = (int64_t)z * g.nxy + sg.rowbase;
+      T fx[CX], fy[CX], fz[CX], dg[CX] = {};
+      int lb[CX];
+      if (sg.own) {
+        pnew_at(z + 1, pn);
+        ld_cells<T, CX, true>(Fx, iz, sg.nv, fx);
+        ld_cells<T, CX, true>(Fy, iz, sg.nv, fy);
+        ld_cells<T, CX, true>(Fz, iz, sg.nv, fz);
+        ld_labels<CX>(a.label, iz, sg.nv, lb);
+        if constexpr (sizeof(T) == 8) ld_cells<T, CX, true>(a.diag64, iz, sg.nv, dg);
+        sm_st<T, CX>(sP + (warp + 1) * RS + HOFF + lane * CX, pc);
+        sm_st<T, CX>(sTy + (warp + 1) * TX + lane * CX, fy);
+        if (lane == 0) {
+          const int x = sg.x0 - 1;
+          const bool ok = x >= 0 && sg.y < g.ny;
+          sP[(warp + 1) * RS + HOFF - 1] = ok ? pnew_scalar(x, z) : T(0);
+          sTxh[warp] = ok ? Fx[(int64_t)z * g.nxy + (int64_t)sg.y * g.nx + x] : T(0);
+        }
+        if (lane == 31) {
+          const int x = sg.x0 + TX;
+          const bool ok = x < g.nx && sg.y < g.ny;
+          sP[(warp + 1) * RS + HOFF + TX] = ok ? pnew_scalar(x, z) : T(0);
+        }
+      } else {
+        T ph[CX];
+        pnew_at(z, ph);
+        const int row = (warp == kTY) ? 0 : kTY + 1;
+        sm_st<T, CX>(sP + row * RS + HOFF + lane * CX, ph);
+        if (warp == kTY) {
+          T ty0[CX];
+          if (sg.nv > 0) ld_cells<T, CX, true>(Fy, iz, sg.nv, ty0);
+          else {
+#pragma unroll
+            for (int c = 0; c < CX; ++c) ty0[c] = T(0);
+          }
+          sm_st<T, CX>(sTy + lane * CX, ty0);
+        }
+      }
+      __syncthreads();
+      if (sg.own) {
+        T left = __shfl_up_sync(kFull, pc[CX - 1], 1);
+        T right = __shfl_down_sync(kFull, pc[0], 1);
+        T txl = __shfl_up_sync(kFull, fx[CX - 1], 1);
+        if (lane == 0) {
+          left = sP[(warp + 1) * RS + HOFF - 1];
+          txl = sTxh[warp];
+        }
+        if (lane == 31) right = sP[(warp + 1) * RS + HOFF + TX];
+        T ym[CX], yp[CX], fym[CX];
+        sm_ld<T, CX>(sP + warp * RS + HOFF + lane * CX, ym);
+        sm_ld<T, CX>(sP + (warp + 2) * RS + HOFF + lane * CX, yp);
+        sm_ld<T, CX>(sTy + warp * TX + lane * CX, fym);
+        const bool dzc = dir_axis(z, g.nz, g.dlo_z, g.dhi_z);
+        const bool dzm = dir_axis(z - 1, g.nz, g.dlo_z, g.dhi_z);
+        const bool dzp = dir_axis(z + 1, g.nz, g.dlo_z, g.dhi_z);
+#pragma unroll
+        for (int c = 0; c < CX; ++c) {
+          const bool valid = c < sg.nv;
+          const T u = pc[c];
+          const T xm = (c > 0) ? pc[(c > 0) ? c - 1 : 0] : left;
+          const T xp = (c < CX - 1) ? pc[(c < CX - 1) ? c + 1 : 0] : right;
+          const T fxm = (c > 0) ? fx[(c > 0) ? c - 1 : 0] : txl;
+          const T v = stencil<T>(dxc[c] || dyc || dzc, u, dg[c], fxm, xm, !dxm[c], fx[c], xp, !dxp[c], fym[c],
+                                 ym[c], !dym, fy[c], yp[c], !dyp, tzm[c], pm[c], !dzm, fz[c], pn[c], !dzp);
+          const int l = valid ? lb[c] : cur;
+          if (__any_sync(kFull, l != cur)) {
+            warp_flush<WACC>(cur, (double)run, sm.acc, d, warp);
+            cur = l;
+            run = T(0);
+          }
+          if (valid) {
+            run += v;
+            gam += u * v;
+          }
+        }
+        st_cells<T, CX>(pnew, iz, sg.nv, pc);
+#pragma unroll
+        for (int c = 0; c < CX; ++c) {
+          pm[c] = pc[c];
+          pc[c] = pn[c];
+          tzm[c] = fz[c];
+        }
+      }
+    }
+    dgam += (double)gam;
+  }
+  if (warp < kTY) warp_flush<WACC>(cur, (double)run, sm.acc, d, warp);
+  const double gsum = block_sum(dgam, sm.red);  // contains __syncthreads
+  for (int k = threadIdx.x; k < d; k += blockDim.x) {
+    double t = 0.0;
+    if constexpr (WACC) {
+      for (int w = 0; w < kTY; ++w) t += sm.acc[w * d + k];
+    } else {
+      t = sm.acc[k];
+    }
+    part_row[k] = t;
+  }
+  if (threadIdx.x == 0) part_row[d + 0] = gsum;
+}
+
+// ---------------------------------------------------------------------------
+// Sweep B: u = p - Z y, w = A u, xhat += alpha p, r = diag z - alpha w,
+// z = r / diag, rho' = r . z, rr = r . r
+// ---------------------------------------------------------------------------
+template <typename T, int CX, bool WACC>
+__device__ void sweep_B(const SolveArgs& a, const Sm<T>& sm, const T* p, T* zb, T* xh, T alpha,
+                        const T* __restrict__ Fx, const T* __restrict__ Fy, const T* __restrict__ Fz,
+                        double* part_row) {
+  using C = Cfg<T, CX, WACC>;
+  constexpr int TX = C::TX, RS = C::RS, HOFF = C::HOFF;
+  const Geo& g = a.g;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const T* Y = sm.Y;
+  double drho = 0.0, drr = 0.0;
+  const int64_t t0 = a.ntiles * blockIdx.x / gridDim.x, t1 = a.ntiles * (blockIdx.x + 1) / gridDim.x;
+  for (int64_t t = t0; t < t1;) {
+    const int64_t ct = t / g.nz;
+    const int z0 = (int)(t % g.nz);
+    const int z1 = (int)((int64_t)g.nz < (int64_t)z0 + (t1 - t) ? (int64_t)g.nz : (int64_t)z0 + (t1 - t));
+    t += z1 - z0;
+    const Seg sg = make_seg<TX>(a, ct, z0, z1, CX);
+    // u = p - y[label] at this lane's cells of plane zz; also returns p
+    auto u_at = [&](int zz, T(&u)[CX], T(&pv)[CX]) {
+      if (zz < 0 || zz >= g.nz || sg.nv == 0) {
+#pragma unroll
+        for (int c = 0; c < CX; ++c) u[c] = pv[c] = T(0);
+        return;
+      }
+      int lb[CX];
+      const int64_t i = (int64_t)zz * g.nxy + sg.rowbase;
+      ld_cells<T, CX, false>(p, i, sg.nv, pv);
+      ld_labels<CX>(a.label, i, sg.nv, lb);
+#pragma unroll
+      for (int c = 0; c < CX; ++c) u[c] = (c < sg.nv) ? pv[c] - Y[lb[c]] : T(0);
+    };
+    auto u_scalar = [&](int x, int zz) -> T {
+      const int64_t i = (int64_t)zz * g.nxy + (int64_t)sg.y * g.nx + x;
+      return p[i] - Y[__ldg(a.label + i)];
+    };
+    T um[CX], uc[CX], un[CX], pcur[CX], pnx[CX], tzm[CX];
+    bool dxc[CX], dxm[CX], dxp[CX];
+#pragma unroll
+    for (int c = 0; c < CX; ++c) {
+      const int x = sg.xl + c;
+      dxc[c] = dir_axis(x, g.nx, g.dlo_x, g.dhi_x);
+      dxm[c] = dir_axis(x - 1, g.nx, g.dlo_x, g.dhi_x);
+      dxp[c] = dir_axis(x + 1, g.nx, g.dlo_x, g.dhi_x);
+    }
+    const bool dyc = dir_axis(sg.y, g.ny, g.dlo_y, g.dhi_y);
+    const bool dym = dir_axis(sg.y - 1, g.ny, g.dlo_y, g.dhi_y);
+    const bool dyp = dir_axis(sg.y + 1, g.ny, g.dlo_y, g.dhi_y);
+    if (sg.own) {
+      T dummy[CX];
+      u_at(z0 - 1, um, dummy);
+      u_at(z0, uc, pcur);
+      if (z0 > 0 && sg.nv > 0) ld_cells<T, CX, true>(Fz, (int64_t)(z0 - 1) * g.nxy + sg.rowbase, sg.nv, tzm);
+      else {
+#pragma unroll
+        for (int c = 0; c < CX; ++c) tzm[c] = T(0);
+      }
+    }
+    T rho = T(0), rr = T(0);
+    for (int z = z0; z < z1; ++z) {
+      const int buf = z & 1;
+      T* sP = sm.P + buf * (kTY + 2) * RS;
+      T* sTy = sm.Ty + buf * (kTY + 1) * TX;
+      T* sTxh = sm.Txh + buf * kTY;
+      const int64_t iz = (int64_t)z * g.nxy + sg.rowbase;
+      T fx[CX], fy[CX], fz[CX], dg[CX] = {}, idg[CX] = {}, zo[CX], xo[CX];
+      if (sg.own) {
+        u_at(z + 1, un, pnx);
+        ld_cells<T, CX, true>(Fx, iz, sg.nv, fx);
+        ld_cells<T, CX, true>(Fy, iz, sg.nv, fy);
+        ld_cells<T, CX, true>(Fz, iz, sg.nv, fz);
+        ld_cells<T, CX, false>(zb, iz, sg.nv, zo);
+        ld_cells<T, CX, false>(xh, iz, sg.nv, xo);
+        if constexpr (sizeof(T) == 8) {
+          ld_cells<T, CX, true>(a.diag64, iz, sg.nv, dg);
+          ld_cells<T, CX, true>(a.invdiag64, iz, sg.nv, idg);
+        }
+        sm_st<T, CX>(sP + (warp + 1) * RS + HOFF + lane * CX, uc);
+        sm_st<T, CX>(sTy + (warp + 1) * TX + lane * CX, fy);
+        if (lane == 0) {
+          const int x = sg.x0 - 1;
+          const bool ok = x >= 0 && sg.y < g.ny;
+          sP[(warp + 1) * RS + HOFF - 1] = ok ? u_scalar(x, z) : T(0);
+          sTxh[warp] = ok ? Fx[(int64_t)z * g.nxy + (int64_t)sg.y * g.nx + x] : T(0);
+        }
+        if (lane == 31) {
+          const int x = sg.x0 + TX;
+          const bool ok = x < g.nx && sg.y < g.ny;
+          sP[(warp + 1) * RS + HOFF + TX] = ok ? u_scalar(x, z) : T(0);
+        }
+      } else {
+        T uh[CX], ph[CX];
+        u_at(z, uh, ph);
+        const int row = (warp == kTY) ? 0 : kTY + 1;
+        sm_st<T, CX>(sP + row * RS + HOFF + lane * CX, uh);
+        if (warp == kTY) {
+          T ty0[CX];
+          if (sg.nv > 0) ld_cells<T, CX, true>(Fy, iz, sg.nv, ty0);
+          else {
+#pragma unroll
+            for (int c = 0; c < CX; ++c) ty0[c] = T(0);
+          }
+          sm_st<T, CX>(sTy + lane * CX, ty0);
+        }
+      }
+      __syncthreads();
+      if (sg.own) {
+        T left = __shfl_up_sync(kFull, uc[CX - 1], 1);
+        T right = __shfl_down_sync(kFull, uc[0], 1);
+        T txl = __shfl_up_sync(kFull, fx[CX - 1], 1);
+        if (lane == 0) {
+          left = sP[(warp + 1) * RS + HOFF - 1];
+          txl = sTxh[warp];
+        }
+        if (lane == 31) right = sP[(warp + 1) * RS + HOFF + TX];
+        T ym[CX], yp[CX], fym[CX];
+        sm_ld<T, CX>(sP + warp * RS + HOFF + lane * CX, ym);
+        sm_ld<T, CX>(sP + (warp + 2) * RS + HOFF + lane * CX, yp);
+        sm_ld<T, CX>(sTy + warp * TX + lane * CX, fym);
+        const bool dzc = dir_axis(z, g.nz, g.dlo_z, g.dhi_z);
+        const bool dzm = dir_axis(z - 1, g.nz, g.dlo_z, g.dhi_z);
+        const bool dzp = dir_axis(z + 1, g.nz, g.dlo_z, g.dhi_z);
+        T zn[CX], xn[CX];
+#pragma unroll
+        for (int c = 0; c < CX; ++c) {
+          const T u = uc[c];
+          const T xm = (c > 0) ? uc[(c > 0) ? c - 1 : 0] : left;
+          const T xp = (c < CX - 1) ? uc[(c < CX - 1) ? c + 1 : 0] : right;
+          const T fxm = (c > 0) ? fx[(c > 0) ? c - 1 : 0] : txl;
+          const bool dirc = dxc[c] || dyc || dzc;
+          T dgi;
+          if constexpr (sizeof(T) == 8) dgi = dg[c];
+          else dgi = dirc ? T(1) : (((((tzm[c] + fym[c]) + fxm) + fx[c]) + fy[c]) + fz[c]);
+          const T w = stencil<T>(dirc, u, dgi, fxm, xm, !dxm[c], fx[c], xp, !dxp[c], fym[c], ym[c], !dym, fy[c],
+                                 yp[c], !dyp, tzm[c], um[c], !dzm, fz[c], un[c], !dzp);
+          const T r = dgi * zo[c] - alpha * w;
+          T znew;
+          if constexpr (sizeof(T) == 8) znew = r * idg[c];
+          else znew = r / dgi;
+          zn[c] = znew;
+          xn[c] = xo[c] + alpha * pcur[c];
+          if (c < sg.nv) {
+            rho += r * znew;
+            rr += r * r;
+          }
+        }
+        st_cells<T, CX>(zb, iz, sg.nv, zn);
+        st_cells<T, CX>(xh, iz, sg.nv, xn);
+#pragma unroll
+        for (int c = 0; c < CX; ++c) {
+          um[c] = uc[c];
+          uc[c] = un[c];
+          pcur[c] = pnx[c];
+          tzm[c] = fz[c];
+        }
+      }
+    }
+    drho += (double)rho;
+    drr += (double)rr;
+  }
+  const double s1 = block_sum(drho, sm.red);
+  const double s2 = block_sum(drr, sm.red);
+  if (threadIdx.x == 0) {
+    part_row[a.d + 1] = s1;
+    part_row[a.d + 2] = s2;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Refinement sweeps (FP64, one thread per cell).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool is_dir_cell(const Geo& g, int ix, int iy, int iz) {
+  return dir_axis(ix, g.nx, g.dlo_x, g.dhi_x) || dir_axis(iy, g.ny, g.dlo_y, g.dhi_y) ||
+         dir_axis(iz, g.nz, g.dlo_z, g.dhi_z);
+}
+
+// (A w)_i in FP64 for the vector given by `val(j)`.
+template <typename F>
+__device__ __forceinline__ double apply64(const SolveArgs& a, int64_t i, int ix, int iy, int iz, F val) {
+  const Geo& g = a.g;
+  if (is_dir_cell(g, ix, iy, iz)) return val(i);
+  double v = a.diag64[i] * val(i);
+  if (ix > 0 && !dir_axis(ix - 1, g.nx, g.dlo_x, g.dhi_x)) v -= a.Tx64[i - 1] * val(i - 1);
+  if (ix + 1 < g.nx && !dir_axis(ix + 1, g.nx, g.dlo_x, g.dhi_x)) v -= a.Tx64[i] * val(i + 1);
+  if (iy > 0 && !dir_axis(iy - 1, g.ny, g.dlo_y, g.dhi_y)) v -= a.Ty64[i - g.nx] * val(i - g.nx);
+  if (iy + 1 < g.ny && !dir_axis(iy + 1, g.ny, g.dlo_y, g.dhi_y)) v -= a.Ty64[i] * val(i + g.nx);
+  if (iz > 0 && !dir_axis(iz - 1, g.nz, g.dlo_z, g.dhi_z)) v -= a.Tz64[i - g.nxy] * val(i - g.nxy);
+  if (iz + 1 < g.nz && !dir_axis(iz + 1, g.nz, g.dlo_z, g.dhi_z)) v -= a.Tz64[i] * val(i + g.nxy);
+  return v;
+}
+
+// O1: r' = b - A (x + xhat), s = Z^T r', ||b||^2
+// The segmented sum groups the lanes of a warp by label (fixed lane order)
+// and, for d <= kWarpAccMaxD, adds each group into the warp's own row of
+// shared accumulators, so the result does not depend on warp scheduling.
+template <typename T, bool WACC>
+__device__ void sweep_O1(const SolveArgs& a, double* sacc, double* red, double* part_row) {
+  const Geo& g = a.g;
+  const int d = a.d;
+  const int warp = threadIdx.x >> 5;
+  const T* xh = static_cast<const T*>(a.xh);
+  for (int k = threadIdx.x; k < (WACC ? kWarps : 1) * d; k += blockDim.x) sacc[k] = 0.0;
+  __syncthreads();
+  double bb = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t nround = (g.n + stride - 1) / stride;
+  for (int64_t rnd = 0; rnd < nround; ++rnd) {
+    const int64_t i = rnd * stride + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool ok = i < g.n;
+    double r = 0.0;
+    int l = -1;
+    if (ok) {
+      const int ix = (int)(i % g.nx), iy = (int)((i / g.nx) % g.ny), iz = (int)(i / g.nxy);
+      const double Aw = apply64(a, i, ix, iy, iz, [&](int64_t j) { return a.x[j] + (double)xh[j]; });
+      const double bi = a.b[i];
+      r = bi - Aw;
+      a.r64[i] = r;
+      bb += bi * bi;
+      l = a.label[i];
+    }
+    warp_flush<WACC>(l, r, sacc, d, warp);
+  }
+  const double bsum = block_sum(bb, red);
+  for (int k = threadIdx.x; k < d; k += blockDim.x) {
+    double t = 0.0;
+    if constexpr (WACC) {
+      for (int w = 0; w < kWarps; ++w) t += sacc[w * d + k];
+    } else {
+      t = sacc[k];
+    }
+    part_row[k] = t;
+  }
+  if (threadIdx.x == 0) part_row[d + 3] = bsum;
+}
+
+// O2: x += xhat + Z y, rhat = r' - A Z y, z = M^{-1} rhat, xhat = p = 0
+template <typename T>
+__device__ void sweep_O2(const SolveArgs& a, const double* Yd, double* red, double* part_row) {
+  const Geo& g = a.g;
+  T* xh = static_cast<T*>(a.xh);
+  T* zb = static_cast<T*>(a.z);
+  T* p0 = static_cast<T*>(a.p0);
+  T* p1 = static_cast<T*>(a.p1);
+  double rr = 0.0, rho = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < g.n; i += stride) {
+    const int ix = (int)(i % g.nx), iy = (int)((i / g.nx) % g.ny), iz = (int)(i / g.nxy);
+    const double AZy = apply64(a, i, ix, iy, iz, [&](int64_t j) { return Yd[__ldg(a.label + j)]; });
+    const double rh = a.r64[i] - AZy;
+    a.x[i] = a.x[i] + (double)xh[i] + Yd[__ldg(a.label + i)];
+    const T zt = (T)(rh * a.invdiag64[i]);
+    zb[i] = zt;
+    xh[i] = T(0);
+    p0[i] = T(0);
+    p1[i] = T(0);
+    rr += rh * rh;
+    rho += rh * (double)zt;
+  }
+  const double s1 = block_sum(rho, red);
+  const double s2 = block_sum(rr, red);
+  if (threadIdx.x == 0) {
+    part_row[a.d + 1] = s1;
+    part_row[a.d + 2] = s2;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Grid-wide phases on the partial sums.
+// ---------------------------------------------------------------------------
+// s_k = sum over CTAs of part[c][k], one warp per column, fixed order.
+__device__ void phase_reduce_s(const SolveArgs& a) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nw = blockDim.x >> 5;
+  const int G = gridDim.x;
+  for (int k = blockIdx.x * nw + warp; k < a.d; k += G * nw) {
+    double t = 0.0;
+    for (int c = lane; c < G; c += 32) t += a.part[(int64_t)c * a.pstride + k];
+    t = warp_sum(t);
+    if (lane == 0) a.s_glob[k] = t;
+  }
+}
+
+// y = E^{-1} s, one warp per row.
+__device__ void phase_coarse(const SolveArgs& a) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nw = blockDim.x >> 5;
+  for (int j = blockIdx.x * nw + warp; j < a.d; j += gridDim.x * nw) {
+    const double* row = a.Einv + (int64_t)j * a.d;
+    double t = 0.0;
+    for (int k = lane; k < a.d; k += 32) t += __ldg(row + k) * a.s_glob[k];
+    t = warp_sum(t);
+    if (lane == 0) a.y_glob[j] = t;
+  }
+}
+
+// Sum of one scalar slot over all CTAs (same order in every CTA).
+__device__ double cta_scalar(const SolveArgs& a, int slot, double* red) {
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = 0.0;
+    for (int c = threadIdx.x; c < (int)gridDim.x; c += 32) t += a.part[(int64_t)c * a.pstride + a.d + slot];
+    t = warp_sum(t);
+    if (threadIdx.x == 0) red[40] = t;
+  }
+  __syncthreads();
+  return red[40];
+}
+
+// s . y (same order in every CTA).
+__device__ double cta_sdoty(const SolveArgs& a, double* red) {
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = 0.0;
+    for (int k = threadIdx.x; k < a.d; k += 32) t += a.s_glob[k] * a.y_glob[k];
+    t = warp_sum(t);
+    if (threadIdx.x == 0) red[41] = t;
+  }
+  __syncthreads();
+  return red[41];
+}
+
+template <typename T, int CX, bool WACC>
+__global__ void __launch_bounds__(kThreads) k_solve(SolveArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const Sm<T> sm = carve<T, CX, WACC>(smem_raw, a.d);
+  double* my_part = a.part + (int64_t)blockIdx.x * a.pstride;
+  unsigned epoch = 0;
+  const double tol2 = a.tol * a.tol;
+  const T* Fx = static_cast<const T*>(a.Txi);
+  const T* Fy = static_cast<const T*>(a.Tyi);
+  const T* Fz = static_cast<const T*>(a.Tzi);
+  T* zb = static_cast<T*>(a.z);
+  T* xh = static_cast<T*>(a.xh);
+  double bb = 0.0, rr_outer = 0.0, rho = 0.0, rec_rr = 0.0;
+  int its = 0, outer = 0, status = 0;
+  bool converged = false;
+  bool failed = false;
+  for (;;) {
+    // ---- refinement step: residual, coarse correction, projection ----
+    sweep_O1<T, WACC>(a, sm.acc, sm.red, my_part);
+    if (!grid_barrier(a.sy, epoch)) { failed = true; break; }
+    phase_reduce_s(a);
+    if (!grid_barrier(a.sy, epoch)) { failed = true; break; }
+    phase_coarse(a);
+    if (!grid_barrier(a.sy, epoch)) { failed = true; break; }
+    if (outer == 0) bb = cta_scalar(a, 3, sm.red);
+    for (int k = threadIdx.x; k < a.d; k += blockDim.x) sm.Yd[k] = a.y_glob[k];
+    __syncthreads();
+    sweep_O2<T>(a, sm.Yd, sm.red, my_part);
+    if (!grid_barrier(a.sy, epoch)) { failed = true; break; }
+    rho = cta_scalar(a, 1, sm.red);
+    rr_outer = cta_scalar(a, 2, sm.red);
+    ++outer;
+    if (!isfinite(rr_outer) || !isfinite(rho)) { status = SLD_ERR_BREAKDOWN; break; }
+    if (a.fp64) {
+      if (outer == 1 && rr_outer <= tol2 * bb) { converged = true; rec_rr = rr_outer; break; }
+      if (outer >= 2) break;  // x = x* + P^T xhat written: done
+    } else {
+      rec_rr = rr_outer;
+      if (rr_outer <= tol2 * bb) { converged = true; break; }
+      if (outer > a.max_outer || its >= a.maxiter) break;
+    }
+    const double tgt2 = a.fp64 ? tol2 * bb : fmax(a.inner_tol * a.inner_tol * rr_outer, 0.09 * tol2 * bb);
+    // ---- inner deflated CG ----
+    double beta = 0.0;
+    T* pold = static_cast<T*>(a.p0);
+    T* pnew = static_cast<T*>(a.p1);
+    for (;;) {
+      sweep_A<T, CX, WACC>(a, sm, zb, pold, pnew, (T)beta, Fx, Fy, Fz, my_part);
+      if (!grid_barrier(a.sy, epoch)) { failed = true; break; }
+      phase_reduce_s(a);
+      if (!grid_barrier(a.sy, epoch)) { failed = true; break; }
+      phase_coarse(a);
+      if (!grid_barrier(a.sy, epoch)) { failed = true; break; }
+      const double gamma = cta_scalar(a, 0, sm.red);
+      const double delta = gamma - cta_sdoty(a, sm.red);
+      if (!(delta > 0.0) || !isfinite(delta) || !isfinite(rho)) {
+        if (a.fp64) status = SLD_ERR_BREAKDOWN;
+        break;
+      }
+      const double alpha = rho / delta;
+      for (int k = threadIdx.x; k < a.d; k += blockDim.x) sm.Y[k] = (T)a.y_glob[k];
+      __syncthreads();
+      sweep_B<T, CX, WACC>(a, sm, pnew, zb, xh, (T)alpha, Fx, Fy, Fz, my_part);
+      if (!grid_barrier(a.sy, epoch)) { failed = true; break; }
+      const double rho_new = cta_scalar(a, 1, sm.red);
+      const double rr = cta_scalar(a, 2, sm.red);
+      ++its;
+      if (a.fp64) rec_rr = rr;
+      if (rr <= tgt2) {
+        if (a.fp64) converged = true;
+        break;
+      }
+      if (its >= a.maxiter) break;
+      beta = rho_new / rho;
+      rho = rho_new;
+      T* tmp = pold;
+      pold = pnew;
+      pnew = tmp;
+    }
+    if (failed || status) break;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.out[kOutIters] = its;
+    a.out[kOutOuter] = outer;
+    a.out[kOutRR] = rr_outer;
+    a.out[kOutBB] = bb;
+    a.out[kOutStatus] = failed ? -1.0 : (status ? (double)status : (converged ? 0.0 : (double)SLD_ERR_NOT_CONVERGED));
+    a.out[kOutRecRR] = rec_rr;
+  }
+}
+
+template <typename T, int CX, bool WACC>
+int launch(sld_system s, SolveArgs& a, const sld_options& o, float* ms, std::string* msg) {
+  const size_t smem = smem_bytes<T, CX, WACC>(a.d);
+  auto kern = k_solve<T, CX, WACC>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) {
+    *msg = std::string("solve kernel attribute: ") + cudaGetErrorString(e);
+    return SLD_ERR_CUDA;
+  }
+  int per = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kThreads, smem);
+  if (per < 1) {
+    *msg = "solve kernel does not fit on an SM";
+    return SLD_ERR_CUDA;
+  }
+  if (o.ctas_per_sm > 0) per = std::min(per, o.ctas_per_sm);
+  int G = s->nsm * per;
+  G = (int)std::max<int64_t>(1, std::min<int64_t>(G, a.ntiles));
+  if (G > s->part_rows) G = s->part_rows;
+  void* args[] = {&a};
+  cudaEventRecord(s->ev0, s->stream);
+  e = cudaLaunchCooperativeKernel((void*)kern, dim3(G), dim3(kThreads), args, smem, s->stream);
+  cudaEventRecord(s->ev1, s->stream);
+  if (e != cudaSuccess) {
+    *msg = std::string("solve launch: ") + cudaGetErrorString(e);
+    return SLD_ERR_CUDA;
+  }
+  e = cudaEventSynchronize(s->ev1);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    *msg = std::string("solve kernel: ") + cudaGetErrorString(e);
+    return SLD_ERR_CUDA;
+  }
+  cudaEventElapsedTime(ms, s->ev0, s->ev1);
+  return SLD_OK;
+}
+
+}  // namespace
+
+int run_solve(sld_system s, const double* b_dev, const sld_options& o, sld_result* res, std::string* msg) {
+  const int64_t n = s->g.n;
+  const bool fp64 = o.precision == SLD_FP64;
+  SolveArgs a{};
+  a.g = s->g;
+  a.cx = (s->g.nx % 4 == 0 && s->g.nx >= 96) ? 4 : 1;
+  const int TX = 32 * a.cx;
+  a.ntx = (s->g.nx + TX - 1) / TX;
+  a.nty = (s->g.ny + kTY - 1) / kTY;
+  a.ntiles = (int64_t)a.ntx * a.nty * s->g.nz;
+  a.d = s->d;
+  a.label = s->label;
+  a.Einv = s->Einv;
+  a.Tx64 = s->Tx;
+  a.Ty64 = s->Ty;
+  a.Tz64 = s->Tz;
+  a.diag64 = s->diag;
+  a.invdiag64 = s->invdiag;
+  a.b = b_dev;
+  a.x = s->x;
+  a.r64 = s->r64;
+  if (fp64) {
+    a.Txi = s->Tx;
+    a.Tyi = s->Ty;
+    a.Tzi = s->Tz;
+  } else {
+    a.Txi = s->Tx32;
+    a.Tyi = s->Ty32;
+    a.Tzi = s->Tz32;
+  }
+  a.z = s->z;
+  a.p0 = s->p0;
+  a.p1 = s->p1;
+  a.xh = s->xh;
+  a.part = s->part;
+  a.pstride = (s->d + kPartScalars + 3) / 4 * 4;
+  a.s_glob = s->s_glob;
+  a.y_glob = s->y_glob;
+  a.out = s->out;
+  a.sy.count = s->bar;
+  a.sy.status = s->status;
+  a.sy.timeout_ns = (unsigned long long)((o.timeout_s > 0 ? o.timeout_s : 2.0) * 1e9);
+  a.sy.skip_epoch = o.debug_skip_barrier >= 0 ? o.debug_skip_barrier + 1 : 0;
+  a.tol = o.tol;
+  a.inner_tol = o.inner_tol;
+  a.maxiter = o.maxiter;
+  a.max_outer = fp64 ? 1 : o.max_outer;
+  a.fp64 = fp64 ? 1 : 0;
+  // x = 0; the inner state is set by the first refinement step
+  cudaMemsetAsync(s->x, 0, sizeof(double) * n, s->stream);
+  cudaMemsetAsync(s->xh, 0, sizeof(double) * n, s->stream);
+  cudaMemsetAsync(s->bar, 0, 64, s->stream);
+  cudaMemsetAsync(s->out, 0, sizeof(double) * kOutCount, s->stream);
+  float ms = 0.f;
+  int st;
+  const bool wacc = s->d <= kWarpAccMaxD;
+  if (fp64) {
+    if (a.cx == 4) st = wacc ? launch<double, 4, true>(s, a, o, &ms, msg) : launch<double, 4, false>(s, a, o, &ms, msg);
+    else st = wacc ? launch<double, 1, true>(s, a, o, &ms, msg) : launch<double, 1, false>(s, a, o, &ms, msg);
+  } else {
+    if (a.cx == 4) st = wacc ? launch<float, 4, true>(s, a, o, &ms, msg) : launch<float, 4, false>(s, a, o, &ms, msg);
+    else st = wacc ? launch<float, 1, true>(s, a, o, &ms, msg) : launch<float, 1, false>(s, a, o, &ms, msg);
+  }
+  if (st != SLD_OK) return st;
+  double out[kOutCount];
+  int dev_status = 0;
+  cudaMemcpyAsync(out, s->out, sizeof(out), cudaMemcpyDeviceToHost, s->stream);
+  cudaMemcpyAsync(&dev_status, s->status, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
+  cudaError_t e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) {
+    *msg = std::string("solve readback: ") + cudaGetErrorString(e);
+    return SLD_ERR_CUDA;
+  }
+  res->iterations = (int)out[kOutIters];
+  res->outer_steps = (int)out[kOutOuter];
+  res->recursive_relres = out[kOutBB] > 0 ? std::sqrt(out[kOutRecRR] / out[kOutBB]) : 0.0;
+  res->solve_ms = ms;
+  if (dev_status != 0) {
+    *msg = dev_status == SLD_ERR_TIMEOUT ? "a device-side wait timed out (grid barrier)" : "device error";
+    return dev_status;
+  }
+  const int code = (int)out[kOutStatus];
+  if (code == SLD_ERR_NOT_CONVERGED) *msg = "not converged within maxiter / max_outer";
+  if (code == SLD_ERR_BREAKDOWN) *msg = "breakdown: p^T P A p <= 0 or a non-finite scalar";
+  return code;
+}
+
+}  // namespace sld

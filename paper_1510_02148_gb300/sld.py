@@ -1,0 +1,234 @@
+"""Python binding of libsld (include/sld.h): argument marshalling only.
+
+Every array may be a numpy array (host) or a torch tensor (host or CUDA);
+the library tells host and device pointers apart.  Nothing here computes
+any step of the method: the library's kernels do.  If libsld.so is missing
+or cannot load, every entry point raises -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsld.so")
+
+OK, ERR_INVALID_ARG, ERR_CUDA, ERR_NOT_CONVERGED, ERR_BREAKDOWN = 0, 1, 2, 3, 4
+ERR_COARSE_SINGULAR, ERR_TIMEOUT, ERR_OOM, ERR_STATE = 5, 6, 7, 8
+STATUS_NAMES = {0: "SLD_OK", 1: "SLD_ERR_INVALID_ARG", 2: "SLD_ERR_CUDA", 3: "SLD_ERR_NOT_CONVERGED",
+                4: "SLD_ERR_BREAKDOWN", 5: "SLD_ERR_COARSE_SINGULAR", 6: "SLD_ERR_TIMEOUT",
+                7: "SLD_ERR_OOM", 8: "SLD_ERR_STATE"}
+FP64, FP32_IR, BF16COEF_IR = 0, 1, 2
+BC_NOFLOW, BC_DIRICHLET = 0, 1
+
+EXPORTED = ["sld_default_options", "sld_build_system", "sld_make_labels", "sld_build_deflation",
+            "sld_solve", "sld_destroy", "sld_last_error", "sld_get_operator", "sld_apply_A",
+            "sld_restrict", "sld_get_coarse"]
+
+
+class SldError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Grid(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int)]
+
+
+class Bc(C.Structure):
+    _fields_ = [("type", C.c_int * 6), ("value", C.c_double * 6)]
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int), ("tol", C.c_double), ("inner_tol", C.c_double),
+                ("maxiter", C.c_int), ("max_outer", C.c_int), ("ctas_per_sm", C.c_int),
+                ("timeout_s", C.c_double), ("debug_skip_barrier", C.c_int)]
+
+
+class Result(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("outer_steps", C.c_int), ("true_relres", C.c_double),
+                ("recursive_relres", C.c_double), ("solve_ms", C.c_double)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(path: str = LIB_PATH):
+    """Load libsld.so (raises if it is missing: build it with __graft_entry__.build())."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"libsld.so not found at {path}; build it first (no CPU fallback)")
+        lib = C.CDLL(path)
+        P = C.c_void_p
+        lib.sld_default_options.argtypes = [C.POINTER(Options)]
+        lib.sld_default_options.restype = None
+        lib.sld_build_system.argtypes = [P, P, Grid, Bc, P, C.POINTER(P)]
+        lib.sld_make_labels.argtypes = [P, C.c_int, C.c_int, C.c_int, P, C.c_int, P]
+        lib.sld_build_deflation.argtypes = [P, P, C.c_int, P, C.c_int, C.c_int]
+        lib.sld_solve.argtypes = [P, P, C.POINTER(Options), P, C.POINTER(Result)]
+        lib.sld_destroy.argtypes = [P]
+        lib.sld_destroy.restype = None
+        lib.sld_last_error.restype = C.c_char_p
+        lib.sld_get_operator.argtypes = [P, P, P, P, P, P]
+        lib.sld_apply_A.argtypes = [P, P, P]
+        lib.sld_restrict.argtypes = [P, P, P]
+        lib.sld_get_coarse.argtypes = [P, P, P]
+        for name in ("sld_build_system", "sld_make_labels", "sld_build_deflation", "sld_solve",
+                     "sld_get_operator", "sld_apply_A", "sld_restrict", "sld_get_coarse"):
+            getattr(lib, name).restype = C.c_int
+        _lib = lib
+        return lib
+
+
+def _check(st: int):
+    if st != OK:
+        raise SldError(st, load().sld_last_error().decode())
+
+
+def _is_torch(a) -> bool:
+    return type(a).__module__.startswith("torch")
+
+
+def _ptr(a, dtype) -> Optional[int]:
+    """Data pointer of a contiguous array of the given numpy dtype (or None)."""
+    if a is None:
+        return None
+    if _is_torch(a):
+        import torch
+        want = {np.float64: torch.float64, np.int32: torch.int32, np.float32: torch.float32}[dtype]
+        if a.dtype != want or not a.is_contiguous():
+            raise TypeError(f"expected a contiguous {want} tensor")
+        return a.data_ptr()
+    if not isinstance(a, np.ndarray) or a.dtype != dtype or not a.flags.c_contiguous:
+        raise TypeError(f"expected a C-contiguous numpy array of {np.dtype(dtype)}")
+    return a.ctypes.data
+
+
+def default_options(**kw) -> Options:
+    o = Options()
+    load().sld_default_options(C.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+@dataclass
+class SolveInfo:
+    iterations: int
+    outer_steps: int
+    true_relres: float
+    recursive_relres: float
+    solve_ms: float
+    status: int
+
+
+class System:
+    """A handle on one assembled pressure system (sld_system)."""
+
+    def __init__(self, K, q=None, bc_type=(1, 1, 0, 0, 0, 0), bc_value=(1.0, 0.0, 0, 0, 0, 0),
+                 stream: Optional[int] = None, shape: Optional[Sequence[int]] = None):
+        lib = load()
+        if shape is None:
+            shape = tuple(K.shape)
+        nz, ny, nx = shape
+        self.shape = (nz, ny, nx)
+        self.n = nx * ny * nz
+        bc = Bc()
+        for f in range(6):
+            bc.type[f] = int(bc_type[f])
+            bc.value[f] = float(bc_value[f])
+        h = C.c_void_p()
+        self._keep = (K, q)
+        _check(lib.sld_build_system(_ptr(K, np.float64), _ptr(q, np.float64), Grid(nx, ny, nz), bc,
+                                    stream, C.byref(h)))
+        self._h = h
+        self.d = 0
+
+    # -- lifetime -------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().sld_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- setup ------------------------------------------------------------
+    def make_labels(self, S, tau, L, out=None):
+        tau_a = np.ascontiguousarray(tau if len(tau) else [0.0], dtype=np.float64)
+        if out is None:
+            out = np.empty(self.n, dtype=np.int32)
+        _check(load().sld_make_labels(self._h, int(S[0]), int(S[1]), int(S[2]), _ptr(tau_a, np.float64),
+                                      int(L), _ptr(out, np.int32)))
+        return out
+
+    def build_deflation(self, d, labels=None):
+        _check(load().sld_build_deflation(self._h, _ptr(labels, np.int32), int(d), None, 0, 0))
+        self.d = int(d)
+
+    # -- solve ------------------------------------------------------------
+    def solve(self, b=None, x=None, options: Optional[Options] = None, raise_on_error=True, **kw):
+        o = options if options is not None else default_options(**kw)
+        if x is None:
+            x = np.empty(self.n, dtype=np.float64)
+        r = Result()
+        st = load().sld_solve(self._h, _ptr(b, np.float64), C.byref(o), _ptr(x, np.float64), C.byref(r))
+        info = SolveInfo(r.iterations, r.outer_steps, r.true_relres, r.recursive_relres, r.solve_ms, st)
+        if st != OK and raise_on_error:
+            _check(st)
+        return x, info
+
+    # -- per-step access ------------------------------------------------------
+    def get_operator(self):
+        arrs = [np.empty(self.n) for _ in range(5)]
+        _check(load().sld_get_operator(self._h, *[a.ctypes.data for a in arrs]))
+        return dict(zip(("Tx", "Ty", "Tz", "diag", "b"), arrs))
+
+    def apply_A(self, x, y=None):
+        if y is None:
+            y = np.empty(self.n)
+        _check(load().sld_apply_A(self._h, _ptr(x, np.float64), _ptr(y, np.float64)))
+        return y
+
+    def restrict(self, v, out=None):
+        if out is None:
+            out = np.empty(self.d)
+        _check(load().sld_restrict(self._h, _ptr(v, np.float64), _ptr(out, np.float64)))
+        return out
+
+    def get_coarse(self):
+        E = np.empty((self.d, self.d))
+        Einv = np.empty((self.d, self.d))
+        _check(load().sld_get_coarse(self._h, E.ctypes.data, Einv.ctypes.data))
+        return E, Einv
+
+
+def from_problem(P, stream=None) -> System:
+    """Build a System (with SLD labels and deflation) from a workloads.Problem."""
+    s = System(np.ascontiguousarray(P.K, dtype=np.float64).reshape(-1),
+               None if P.q is None else np.ascontiguousarray(P.q, dtype=np.float64).reshape(-1),
+               P.bc_type, P.bc_value, stream=stream, shape=P.shape)
+    s.make_labels(P.S, P.tau, P.L)
+    s.build_deflation(P.d)
+    return s
