@@ -31,11 +31,12 @@ sys.path.insert(0, ROOT)
 
 METRIC = "time-to-1e-9 rel. residual & HBM GB/s: mixed/learned/batched vs plain FP64"
 WORKLOAD = "lognormal-layered 256x256x128, point source, 4x4x4 subdomains x 2 levelsets (d=128), tol 1e-9"
-# algorithmic bytes per cell: one FP32 inner iteration (sweeps
-# A and B) and one FP64 refinement step (sweeps O1 and O2)
-BYTES_ITER_FP32 = 64
-BYTES_ITER_FP64 = 120 + 16  # + stored diagonal and inverse diagonal, read once per sweep
-BYTES_OUTER = 152
+# algorithmic bytes per cell: one inner iteration (sweeps A
+# and B) and one FP64 refinement step (sweeps O1 and O2).  The TMA sweeps
+# stream 16-bit labels.
+BYTES_ITER_FP32 = 60   # A: z, p_old, 3 faces, label, p_new  B: p, label, 3 faces, z r/w, xhat r/w
+BYTES_ITER_FP64 = 140  # same vectors and faces in FP64 + diag (A, B) and 1/diag (B)
+BYTES_OUTER = 152      # O1: x, xhat, b, faces, diag, label, r'  O2: r', label, faces, diag, x r/w, xhat r/w, 1/diag, z, p0, p1
 
 
 def _peaks():
@@ -265,7 +266,7 @@ def main():
         "setup_ms": setup_ms,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": None,
-                     "kernel": "k_solve<float,4,true> (persistent)", "peak_kind": peak_kind},
+                     "kernel": "k_solve_tma<float,16,3,true> (persistent, cooperative)", "peak_kind": peak_kind},
         "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(Kh.numel() * 8 + qh.numel() * 8),
                 "d2h_bytes_per_step": int(xh.numel() * 8),
                 "what": "sld_build_system(host K, q) + make_labels + build_deflation + sld_solve -> host x"},

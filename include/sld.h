@@ -101,6 +101,7 @@ typedef struct {
   double true_relres;      /* ||b - A x||_2 / ||b||_2, recomputed in FP64 after the solve */
   double recursive_relres; /* the iteration's own deflated residual at exit, / ||b|| */
   double solve_ms;         /* device time of the persistent solve kernel (CUDA events) */
+  int kernel_path;         /* 1: TMA-pipelined sweeps (nx % 8 == 0), 0: register/shuffle sweeps */
 } sld_result;
 
 /* Fill *o with the defaults listed above. */

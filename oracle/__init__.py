@@ -199,8 +199,11 @@ def dpcg(A: CSR, label=None, d=0, b=None, tol=1e-9, maxiter=20000, Zd=None,
     st = _load().oracle_dpcg(A.n, _p(A.rowptr), _p(A.col), _p(A.val), _p(b), _p(lab), d,
                              _p(Zd), k, float(tol), int(maxiter), _p(x), C.byref(it),
                              C.byref(rr), _p(hist), C.byref(zt))
-    if st not in (OK, ERR_NOT_CONVERGED):
+    if st not in (OK, ERR_NOT_CONVERGED, ERR_BREAKDOWN):
         raise RuntimeError(f"oracle_dpcg failed with status {st}")
+    # ERR_BREAKDOWN (p^T w <= 0) only happens at the roundoff floor of a
+    # tolerance tighter than FP64 can reach; x is then the last iterate and
+    # the caller sees the status.
     if hist is not None:
         hist = hist[: it.value + 1]
     return Result(x, it.value, rr.value, st, hist, zt.value)

@@ -265,6 +265,8 @@ sld_status sld_build_deflation(sld_system s, const int32_t* labels, int d, const
   int bad = 0;
   if ((e = sld::launch_coarse_E(s, &bad)) != cudaSuccess) return cuda_fail(e, "coarse matrix");
   if (bad) return fail(SLD_ERR_INVALID_ARG, "a label is outside [0, d)");
+  if (!s->label16 && (e = dalloc(&s->label16, s->g.n)) != cudaSuccess) return cuda_fail(e, "alloc labels16");
+  if ((e = sld::launch_labels16(s)) != cudaSuccess) return cuda_fail(e, "labels16");
   std::string msg;
   const int st = sld::coarse_factor(s, 2.0, &msg);
   if (st != SLD_OK) return fail((sld_status)st, msg);
@@ -322,7 +324,7 @@ void sld_destroy(sld_system s) {
   if (!s) return;
   if (s->stream) cudaStreamSynchronize(s->stream);
   void* ptrs[] = {s->K, s->Tx, s->Ty, s->Tz, s->diag, s->invdiag, s->b, s->Tx32, s->Ty32, s->Tz32,
-                  s->label, s->E, s->Einv, s->x, s->r64, s->bwork, s->z, s->p0, s->p1, s->xh,
+                  s->label, s->label16, s->E, s->Einv, s->x, s->r64, s->bwork, s->z, s->p0, s->p1, s->xh,
                   s->part, s->s_glob, s->y_glob, s->out, s->bar, s->status};
   for (void* p : ptrs) dfree(p);
   if (s->ev0) cudaEventDestroy(s->ev0);

@@ -42,6 +42,7 @@ struct SolveArgs {
   int64_t ntiles;         // ntx * nty * nz plane-tiles
   int d;
   const int32_t* label;
+  const uint16_t* label16;  // the same labels as 16-bit (streamed by the TMA sweeps)
   const double* Einv;     // d x d
   // FP64 operator
   const double *Tx64, *Ty64, *Tz64, *diag64, *invdiag64, *b;
@@ -81,6 +82,7 @@ struct sld_system_s {
   float *Tx32 = nullptr, *Ty32 = nullptr, *Tz32 = nullptr;
   // deflation
   int32_t* label = nullptr;
+  uint16_t* label16 = nullptr;
   int d = 0, have_labels_d = 0;
   double *E = nullptr, *Einv = nullptr;
   bool deflation_ready = false;
@@ -101,10 +103,14 @@ cudaError_t launch_labels(sld_system s, int Sx, int Sy, int Sz, const double* ta
 cudaError_t launch_coarse_E(sld_system s, int* bad_label);
 int coarse_factor(sld_system s, double timeout_s, std::string* msg);  // returns sld_status
 cudaError_t launch_quantize_fp32(sld_system s);
+cudaError_t launch_labels16(sld_system s);
 cudaError_t launch_apply_A(sld_system s, const double* x, double* y);
 cudaError_t launch_restrict(sld_system s, const double* v, double* out);
 cudaError_t launch_residual(sld_system s, const double* b, const double* x, double* partial_out,
                             double* rr_host, double* bb_host);
+// sld_solve_tma.cu
+bool tma_eligible(const Geo& g);
+int launch_solve_tma(sld_system s, SolveArgs& a, const sld_options& o, float* ms, std::string* msg);
 // sld_solve.cu
 int run_solve(sld_system s, const double* b_dev, const sld_options& o, sld_result* res,
               std::string* msg);  // returns sld_status

@@ -249,6 +249,12 @@ __global__ void k_convert(int64_t n, const double* __restrict__ a, Tout* __restr
   if (i < n) o[i] = (Tout)a[i];
 }
 
+// 16-bit copy of the labels (d <= 65535), streamed by the TMA sweeps.
+__global__ void k_convert_labels(int64_t n, const int32_t* __restrict__ a, uint16_t* __restrict__ o) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) o[i] = (uint16_t)a[i];
+}
+
 // y = A x, FP64, one thread per cell.
 __global__ void k_apply_A(Geo g, const double* __restrict__ Tx, const double* __restrict__ Ty,
                           const double* __restrict__ Tz, const double* __restrict__ diag,
@@ -456,6 +462,12 @@ cudaError_t launch_quantize_fp32(sld_system s) {
   k_convert<float><<<blocks_for(n, 256), 256, 0, s->stream>>>(n, s->Tx, s->Tx32);
   k_convert<float><<<blocks_for(n, 256), 256, 0, s->stream>>>(n, s->Ty, s->Ty32);
   k_convert<float><<<blocks_for(n, 256), 256, 0, s->stream>>>(n, s->Tz, s->Tz32);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_labels16(sld_system s) {
+  const int64_t n = s->g.n;
+  k_convert_labels<<<blocks_for(n, 256), 256, 0, s->stream>>>(n, s->label, s->label16);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,337 @@
+// sld_solve_common.cuh -- device code shared by the two implementations of
+// the persistent SLD-DPCG solve (sld_solve.cu: register/shuffle z-march for
+// any grid; sld_solve_tma.cu: TMA-pipelined z-march for aligned grids): the
+// FP64 refinement sweeps, the grid-wide reduction and coarse-solve phases, the
+// 7-point operator, the label accumulators and the solve's control flow.
+//
+// Control flow (the CG form of the deflated solve of Section 3.1, Def. 3.1,
+// with P = I - A Z E^{-1} Z^T and M = diag A):
+//   refinement step  O1: r' = b - A (x + xhat), s = Z^T r'
+//                    y = E^{-1} s
+//                    O2: x += xhat + Z y, rhat = r' - A Z y (= P r'), z = M^{-1} rhat
+//   With x = 0 this gives x = Z E^{-1} Z^T b (x*) and rhat_0 = P b; after an
+//   inner solve it gives x = x* + P^T xhat (eq. (projectback)).
+//   inner iteration  A : p = z + beta p, v = A p, s = Z^T v, gamma = p.v
+//                    y = E^{-1} s, delta = gamma - s.y (= p.P A p), alpha = rho/delta
+//                    B : w = A (p - Z y) (= P A p), xhat += alpha p,
+//                        r = diag z - alpha w, z = r / diag, rho' = r.z, rr = r.r
+#pragma once
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "sld_device.cuh"
+#include "sld_internal.h"
+
+namespace sld {
+namespace {
+
+// Block-wide sum of one double per thread (fixed order); result to all threads.
+__device__ double block_sum(double v, double* red) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  v = warp_sum(v);
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+  return t;
+}
+
+// Flush the per-lane run sums of a warp into the shared label accumulators.
+// Lanes are grouped by label; each group is summed in lane order and added
+// once by its lowest lane, so no two lanes of a warp write the same slot.
+template <bool WACC>
+__device__ __forceinline__ void warp_flush(int cur, double acc, double* sacc, int d, int warp) {
+  const int lane = threadIdx.x & 31;
+  const unsigned grp = __match_any_sync(kFull, cur);
+  double sum = 0.0;
+#pragma unroll 4
+  for (int src = 0; src < 32; ++src) {
+    const double v = __shfl_sync(kFull, acc, src);
+    if ((grp >> src) & 1u) sum += v;
+  }
+  if (cur >= 0 && lane == __ffs(grp) - 1) {
+    if constexpr (WACC) sacc[warp * d + cur] += sum;
+    else atomicAdd(&sacc[cur], sum);
+  }
+}
+
+// The 7-point operator at one free or Dirichlet cell.
+//   FP32 inner form: sum over faces T (u_i - m_j u_j)  (m_j = 0 for a Dirichlet
+//   neighbour), exact zero row sums, no cancellation of diag * u against the
+//   neighbour sum.  FP64 form: diag u_i - sum m_j T u_j with the stored diagonal.
+template <typename T>
+__device__ __forceinline__ T stencil(bool dirc, T u, T dg, T fxm, T xm, bool mxm, T fxp, T xp, bool mxp, T fym,
+                                     T ym, bool mym, T fyp, T yp, bool myp, T fzm, T zm, bool mzm, T fzp, T zp,
+                                     bool mzp) {
+  if (dirc) return u;
+  if constexpr (sizeof(T) == 8) {
+    T s = dg * u;
+    s -= fxm * (mxm ? xm : T(0));
+    s -= fxp * (mxp ? xp : T(0));
+    s -= fym * (mym ? ym : T(0));
+    s -= fyp * (myp ? yp : T(0));
+    s -= fzm * (mzm ? zm : T(0));
+    s -= fzp * (mzp ? zp : T(0));
+    return s;
+  } else {
+    T s = fxm * (u - (mxm ? xm : T(0)));
+    s += fxp * (u - (mxp ? xp : T(0)));
+    s += fym * (u - (mym ? ym : T(0)));
+    s += fyp * (u - (myp ? yp : T(0)));
+    s += fzm * (u - (mzm ? zm : T(0)));
+    s += fzp * (u - (mzp ? zp : T(0)));
+    return s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Refinement sweeps (FP64, one thread per cell).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool is_dir_cell(const Geo& g, int ix, int iy, int iz) {
+  return dir_axis(ix, g.nx, g.dlo_x, g.dhi_x) || dir_axis(iy, g.ny, g.dlo_y, g.dhi_y) ||
+         dir_axis(iz, g.nz, g.dlo_z, g.dhi_z);
+}
+
+// (A w)_i in FP64 for the vector given by `val(j)`.
+template <typename F>
+__device__ __forceinline__ double apply64(const SolveArgs& a, int64_t i, int ix, int iy, int iz, F val) {
+  const Geo& g = a.g;
+  if (is_dir_cell(g, ix, iy, iz)) return val(i);
+  double v = a.diag64[i] * val(i);
+  if (ix > 0 && !dir_axis(ix - 1, g.nx, g.dlo_x, g.dhi_x)) v -= a.Tx64[i - 1] * val(i - 1);
+  if (ix + 1 < g.nx && !dir_axis(ix + 1, g.nx, g.dlo_x, g.dhi_x)) v -= a.Tx64[i] * val(i + 1);
+  if (iy > 0 && !dir_axis(iy - 1, g.ny, g.dlo_y, g.dhi_y)) v -= a.Ty64[i - g.nx] * val(i - g.nx);
+  if (iy + 1 < g.ny && !dir_axis(iy + 1, g.ny, g.dlo_y, g.dhi_y)) v -= a.Ty64[i] * val(i + g.nx);
+  if (iz > 0 && !dir_axis(iz - 1, g.nz, g.dlo_z, g.dhi_z)) v -= a.Tz64[i - g.nxy] * val(i - g.nxy);
+  if (iz + 1 < g.nz && !dir_axis(iz + 1, g.nz, g.dlo_z, g.dhi_z)) v -= a.Tz64[i] * val(i + g.nxy);
+  return v;
+}
+
+// O1: r' = b - A (x + xhat), s = Z^T r', ||b||^2
+// The segmented sum groups the lanes of a warp by label (fixed lane order)
+// and, for d <= kWarpAccMaxD, adds each group into the warp's own row of
+// shared accumulators, so the result does not depend on warp scheduling.
+template <typename T, bool WACC>
+__device__ void sweep_O1(const SolveArgs& a, double* sacc, double* red, double* part_row) {
+  const Geo& g = a.g;
+  const int d = a.d;
+  const int warp = threadIdx.x >> 5;
+  const T* xh = static_cast<const T*>(a.xh);
+  for (int k = threadIdx.x; k < (WACC ? kWarps : 1) * d; k += blockDim.x) sacc[k] = 0.0;
+  __syncthreads();
+  double bb = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t nround = (g.n + stride - 1) / stride;
+  for (int64_t rnd = 0; rnd < nround; ++rnd) {
+    const int64_t i = rnd * stride + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool ok = i < g.n;
+    double r = 0.0;
+    int l = -1;
+    if (ok) {
+      const int ix = (int)(i % g.nx), iy = (int)((i / g.nx) % g.ny), iz = (int)(i / g.nxy);
+      const double Aw = apply64(a, i, ix, iy, iz, [&](int64_t j) { return a.x[j] + (double)xh[j]; });
+      const double bi = a.b[i];
+      r = bi - Aw;
+      a.r64[i] = r;
+      bb += bi * bi;
+      l = a.label[i];
+    }
+    warp_flush<WACC>(l, r, sacc, d, warp);
+  }
+  const double bsum = block_sum(bb, red);
+  for (int k = threadIdx.x; k < d; k += blockDim.x) {
+    double t = 0.0;
+    if constexpr (WACC) {
+      for (int w = 0; w < kWarps; ++w) t += sacc[w * d + k];
+    } else {
+      t = sacc[k];
+    }
+    part_row[k] = t;
+  }
+  if (threadIdx.x == 0) part_row[d + 3] = bsum;
+}
+
+// O2: x += xhat + Z y, rhat = r' - A Z y, z = M^{-1} rhat, xhat = p = 0
+template <typename T>
+__device__ void sweep_O2(const SolveArgs& a, const double* Yd, double* red, double* part_row) {
+  const Geo& g = a.g;
+  T* xh = static_cast<T*>(a.xh);
+  T* zb = static_cast<T*>(a.z);
+  T* p0 = static_cast<T*>(a.p0);
+  T* p1 = static_cast<T*>(a.p1);
+  double rr = 0.0, rho = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < g.n; i += stride) {
+    const int ix = (int)(i % g.nx), iy = (int)((i / g.nx) % g.ny), iz = (int)(i / g.nxy);
+    const double AZy = apply64(a, i, ix, iy, iz, [&](int64_t j) { return Yd[__ldg(a.label + j)]; });
+    const double rh = a.r64[i] - AZy;
+    a.x[i] = a.x[i] + (double)xh[i] + Yd[__ldg(a.label + i)];
+    const T zt = (T)(rh * a.invdiag64[i]);
+    zb[i] = zt;
+    xh[i] = T(0);
+    p0[i] = T(0);
+    p1[i] = T(0);
+    rr += rh * rh;
+    rho += rh * (double)zt;
+  }
+  fence_proxy_async();  // z, xhat, p stores before the next sweep's TMA reads
+  const double s1 = block_sum(rho, red);
+  const double s2 = block_sum(rr, red);
+  if (threadIdx.x == 0) {
+    part_row[a.d + 1] = s1;
+    part_row[a.d + 2] = s2;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Grid-wide phases on the partial sums.
+// ---------------------------------------------------------------------------
+// s_k = sum over CTAs of part[c][k], one warp per column, fixed order.
+__device__ void phase_reduce_s(const SolveArgs& a) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nw = blockDim.x >> 5;
+  const int G = gridDim.x;
+  for (int k = blockIdx.x * nw + warp; k < a.d; k += G * nw) {
+    double t = 0.0;
+    for (int c = lane; c < G; c += 32) t += a.part[(int64_t)c * a.pstride + k];
+    t = warp_sum(t);
+    if (lane == 0) a.s_glob[k] = t;
+  }
+}
+
+// y = E^{-1} s, one warp per row.
+__device__ void phase_coarse(const SolveArgs& a) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nw = blockDim.x >> 5;
+  for (int j = blockIdx.x * nw + warp; j < a.d; j += gridDim.x * nw) {
+    const double* row = a.Einv + (int64_t)j * a.d;
+    double t = 0.0;
+    for (int k = lane; k < a.d; k += 32) t += __ldg(row + k) * a.s_glob[k];
+    t = warp_sum(t);
+    if (lane == 0) a.y_glob[j] = t;
+  }
+}
+
+// Sum of one scalar slot over all CTAs (same order in every CTA).
+__device__ double cta_scalar(const SolveArgs& a, int slot, double* red) {
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = 0.0;
+    for (int c = threadIdx.x; c < (int)gridDim.x; c += 32) t += a.part[(int64_t)c * a.pstride + a.d + slot];
+    t = warp_sum(t);
+    if (threadIdx.x == 0) red[40] = t;
+  }
+  __syncthreads();
+  return red[40];
+}
+
+// s . y (same order in every CTA).
+__device__ double cta_sdoty(const SolveArgs& a, double* red) {
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = 0.0;
+    for (int k = threadIdx.x; k < a.d; k += 32) t += a.s_glob[k] * a.y_glob[k];
+    t = warp_sum(t);
+    if (threadIdx.x == 0) red[41] = t;
+  }
+  __syncthreads();
+  return red[41];
+}
+
+
+// ---------------------------------------------------------------------------
+// The solve's control flow, shared by the sweep implementations.
+//   sweepA(pold, beta, part) : p_new = z + beta p[pold] into p[pold ^ 1],
+//                              v = A p_new, s = Z^T v, gamma   (part row)
+//   sweepB(pnew, alpha, part): u = p[pnew] - Z y, w = A u, xhat, z, rho', rr
+// Each returns false if a bounded wait inside it gave up.
+// All decisions use scalars every CTA reduces in the same order, so every
+// CTA takes the same branches.
+// ---------------------------------------------------------------------------
+template <typename T, bool WACC, class SweepA, class SweepB>
+__device__ void solve_body(const SolveArgs& a, double* acc, double* Yd, T* Y, double* red, SweepA&& sweepA,
+                           SweepB&& sweepB) {
+  double* my_part = a.part + (int64_t)blockIdx.x * a.pstride;
+  unsigned epoch = 0;
+  const double tol2 = a.tol * a.tol;
+  double bb = 0.0, rr_outer = 0.0, rho = 0.0, rec_rr = 0.0;
+  int its = 0, outer = 0, status = 0;
+  bool converged = false;
+  bool failed = false;
+  for (;;) {
+    // ---- refinement step: residual, coarse correction, projection ----
+    sweep_O1<T, WACC>(a, acc, red, my_part);
+    if (!grid_barrier(a.sy, epoch)) { failed = true; break; }
+    phase_reduce_s(a);
+    if (!grid_barrier(a.sy, epoch)) { failed = true; break; }
+    phase_coarse(a);
+    if (!grid_barrier(a.sy, epoch)) { failed = true; break; }
+    if (outer == 0) bb = cta_scalar(a, 3, red);
+    for (int k = threadIdx.x; k < a.d; k += blockDim.x) Yd[k] = a.y_glob[k];
+    __syncthreads();
+    sweep_O2<T>(a, Yd, red, my_part);
+    if (!grid_barrier(a.sy, epoch)) { failed = true; break; }
+    rho = cta_scalar(a, 1, red);
+    rr_outer = cta_scalar(a, 2, red);
+    ++outer;
+    if (!isfinite(rr_outer) || !isfinite(rho)) { status = SLD_ERR_BREAKDOWN; break; }
+    if (a.fp64) {
+      if (outer == 1 && rr_outer <= tol2 * bb) { converged = true; rec_rr = rr_outer; break; }
+      if (outer >= 2) break;  // x = x* + P^T xhat written: done
+    } else {
+      rec_rr = rr_outer;
+      if (rr_outer <= tol2 * bb) { converged = true; break; }
+      if (outer > a.max_outer || its >= a.maxiter) break;
+    }
+    const double tgt2 = a.fp64 ? tol2 * bb : fmax(a.inner_tol * a.inner_tol * rr_outer, 0.09 * tol2 * bb);
+    // ---- inner deflated CG ----
+    double beta = 0.0;
+    int pold = 0;
+    for (;;) {
+      if (!sweepA(pold, (T)beta, my_part)) { failed = true; break; }
+      if (!grid_barrier(a.sy, epoch)) { failed = true; break; }
+      phase_reduce_s(a);
+      if (!grid_barrier(a.sy, epoch)) { failed = true; break; }
+      phase_coarse(a);
+      if (!grid_barrier(a.sy, epoch)) { failed = true; break; }
+      const double gamma = cta_scalar(a, 0, red);
+      const double delta = gamma - cta_sdoty(a, red);
+      if (!(delta > 0.0) || !isfinite(delta) || !isfinite(rho)) {
+        if (a.fp64) status = SLD_ERR_BREAKDOWN;
+        break;
+      }
+      const double alpha = rho / delta;
+      for (int k = threadIdx.x; k < a.d; k += blockDim.x) Y[k] = (T)a.y_glob[k];
+      __syncthreads();
+      if (!sweepB(pold ^ 1, (T)alpha, my_part)) { failed = true; break; }
+      if (!grid_barrier(a.sy, epoch)) { failed = true; break; }
+      const double rho_new = cta_scalar(a, 1, red);
+      const double rr = cta_scalar(a, 2, red);
+      ++its;
+      if (a.fp64) rec_rr = rr;
+      if (rr <= tgt2) {
+        if (a.fp64) converged = true;
+        break;
+      }
+      if (its >= a.maxiter) break;
+      beta = rho_new / rho;
+      rho = rho_new;
+      pold ^= 1;
+    }
+    if (failed || status) break;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.out[kOutIters] = its;
+    a.out[kOutOuter] = outer;
+    a.out[kOutRR] = rr_outer;
+    a.out[kOutBB] = bb;
+    a.out[kOutStatus] = failed ? -1.0 : (status ? (double)status : (converged ? 0.0 : (double)SLD_ERR_NOT_CONVERGED));
+    a.out[kOutRecRR] = rec_rr;
+  }
+}
+
+}  // namespace
+}  // namespace sld

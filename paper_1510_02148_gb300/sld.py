@@ -53,7 +53,7 @@ class Options(C.Structure):
 
 class Result(C.Structure):
     _fields_ = [("iterations", C.c_int), ("outer_steps", C.c_int), ("true_relres", C.c_double),
-                ("recursive_relres", C.c_double), ("solve_ms", C.c_double)]
+                ("recursive_relres", C.c_double), ("solve_ms", C.c_double), ("kernel_path", C.c_int)]
 
 
 _lib = None
@@ -132,6 +132,7 @@ class SolveInfo:
     recursive_relres: float
     solve_ms: float
     status: int
+    kernel_path: int = 0
 
 
 class System:
@@ -194,7 +195,8 @@ class System:
             x = np.empty(self.n, dtype=np.float64)
         r = Result()
         st = load().sld_solve(self._h, _ptr(b, np.float64), C.byref(o), _ptr(x, np.float64), C.byref(r))
-        info = SolveInfo(r.iterations, r.outer_steps, r.true_relres, r.recursive_relres, r.solve_ms, st)
+        info = SolveInfo(r.iterations, r.outer_steps, r.true_relres, r.recursive_relres, r.solve_ms, st,
+                         r.kernel_path)
         if st != OK and raise_on_error:
             _check(st)
         return x, info

@@ -125,7 +125,8 @@ def _relerr(x, y):
 
 @pytest.mark.parametrize("name,P", CASES, ids=[c[0] for c in CASES])
 @pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "fp32ir"])
-def test_solve_parity(sld, oracle_mod, name, P, precision):
+@pytest.mark.parametrize("path", ["auto", "generic"])
+def test_solve_parity(sld, oracle_mod, name, P, precision, path, monkeypatch):
     """FP64: the same iteration as the oracle, so the solution is within 1e-7
     (relative, 2-norm) of the oracle's at tol 1e-9 and the iteration count
     within 2.  FP32-inner/FP64-refined: a different iteration reaching the
@@ -136,11 +137,16 @@ def test_solve_parity(sld, oracle_mod, name, P, precision):
     A, lab = _oracle_setup(oracle_mod, P)
     ref = oracle_mod.dpcg(A, lab, P.d, tol=P.tol)
     assert ref.status == 0
+    if path == "generic":
+        monkeypatch.setenv("SLD_SOLVER_PATH", "generic")
     s = sld.from_problem(P)
     x, info = s.solve(precision=precision, tol=P.tol)
+    nx = P.shape[2]
+    assert info.kernel_path == (1 if (path == "auto" and nx % 8 == 0) else 0)
     err = _relerr(x, ref.x)
     true = np.linalg.norm(A.b - A.spmv(x)) / np.linalg.norm(A.b)
-    assert abs(true - info.true_relres) <= 1e-3 * true + 1e-14
+    # two FP64 residual evaluations agree to roundoff (~1e-12 near convergence floors)
+    assert abs(true - info.true_relres) <= 1e-3 * true + 1e-12
     if precision == 0:
         assert err <= 1e-7, err
         assert abs(info.iterations - ref.iterations) <= 2, (info.iterations, ref.iterations)
@@ -173,11 +179,13 @@ def test_solve_given_rhs_and_device_buffers(sld, oracle_mod):
     s.close()
 
 
-def test_repeat_solves_identical(sld):
+@pytest.mark.parametrize("precision", [0, 1])
+def test_repeat_solves_identical(sld, precision):
+    """Solves are bitwise repeatable (fixed-order reductions, d <= 256)."""
     P = W.lognormal_point_source(64, 64, 32, 4, (2, 2, 2), seed=3)
     s = sld.from_problem(P)
-    x1, i1 = s.solve(precision=0)
-    x2, i2 = s.solve(precision=0)
+    x1, i1 = s.solve(precision=precision)
+    x2, i2 = s.solve(precision=precision)
     assert i1.iterations == i2.iterations
     assert np.array_equal(x1, x2)
     s.close()
