@@ -193,6 +193,34 @@ sld_status sld_restrict(sld_system s, const double* v, double* out);
 /* Copy out E (d*d, row-major) and E^{-1} (d*d); either may be NULL. */
 sld_status sld_get_coarse(sld_system s, double* E, double* Einv);
 
+/* ---------------------------------------------------------------------- */
+/* Allocation-free variant.                                               */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * out = Z^T v, like sld_restrict, but without allocating any device memory
+ * (no cudaMalloc, cudaFree or allocating library call).  The paper has no
+ * counterpart: this exists for callers that cannot allocate -- processes
+ * whose device memory is already handed to another allocator (a framework's
+ * pool or arena, a hard memory cap) and loops that must not pay for
+ * cudaMalloc / cudaFree, which can block and (cudaFree) synchronise the
+ * device.
+ *   v: n values in device memory; out: d values in device memory (host
+ *   pointers are rejected: staging them would need a buffer).  d <= 1024.
+ *   The handle's device must be the current device.
+ * Work runs on the handle's stream and is asynchronous: out is valid once
+ * that stream has reached the call.  The partial sums go to a fixed 1 MiB
+ * __device__ array (128 CTAs x 1024 labels) that every GPU loading the
+ * library keeps until the process exits.  The first call on a device looks
+ * up that array's device address (cudaGetSymbolAddress) with the device
+ * current; make that first call before any stream capture.  Every call
+ * shares the array and overwrites what it reads, so calls whose kernels
+ * overlap on the GPU (other streams, other host threads) race.
+ * Errors: SLD_ERR_INVALID_ARG (d > 1024, host pointer, wrong current
+ * device), SLD_ERR_STATE (no deflation built), SLD_ERR_CUDA.
+ */
+sld_status sld_restrict_noalloc(sld_system s, const double* v, double* out);
+
 #ifdef __cplusplus
 }
 #endif

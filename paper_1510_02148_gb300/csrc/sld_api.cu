@@ -95,6 +95,10 @@ sld_status ensure_workspace(sld_system s, bool need_fp32) {
 
 }  // namespace
 
+namespace sld {
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace sld
+
 extern "C" {
 
 void sld_default_options(sld_options* o) {

@@ -111,6 +111,8 @@ cudaError_t launch_residual(sld_system s, const double* b, const double* x, doub
 // sld_solve_tma.cu
 bool tma_eligible(const Geo& g);
 int launch_solve_tma(sld_system s, SolveArgs& a, const sld_options& o, float* ms, std::string* msg);
+// sld_api.cu: the thread-local message returned by sld_last_error()
+void set_last_error(const std::string& msg);
 // sld_solve.cu
 int run_solve(sld_system s, const double* b_dev, const sld_options& o, sld_result* res,
               std::string* msg);  // returns sld_status
