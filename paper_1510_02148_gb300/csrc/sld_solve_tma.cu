@@ -49,12 +49,16 @@ struct TCfg {
                           A_FZ = A_FY + al(bY), A_LB = A_FZ + al(bO), A_DG = A_LB + al(bLO),
                           A_END = A_DG + (kDiag ? al(bO) : 0);
   static constexpr unsigned TX_A = unsigned(2 * bH + bX + bY + bO + bLO + (kDiag ? bO : 0));
-  // sweep B slot: p(h) labels(h) Fx Fy Fz z xhat [diag, 1/diag]
+  // sweep B slot: p(h) labels(h) Fx Fy Fz z xhat [diag, 1/diag].  In the FP64
+  // form the own z and xhat are read straight from global memory instead, so
+  // that three slots of the wider FP64 boxes fit two CTAs per SM.
+  static constexpr bool kOwnRing = !kDiag;  // own z, xhat through the ring
   static constexpr size_t B_P = 0, B_LB = al(bH), B_FX = B_LB + al(bLH), B_FY = B_FX + al(bX),
-                          B_FZ = B_FY + al(bY), B_ZO = B_FZ + al(bO), B_XO = B_ZO + al(bO),
-                          B_DG = B_XO + al(bO), B_IDG = B_DG + (kDiag ? al(bO) : 0),
+                          B_FZ = B_FY + al(bY), B_ZO = B_FZ + al(bO), B_XO = B_ZO + (kOwnRing ? al(bO) : 0),
+                          B_DG = B_XO + (kOwnRing ? al(bO) : 0), B_IDG = B_DG + (kDiag ? al(bO) : 0),
                           B_END = B_IDG + (kDiag ? al(bO) : 0);
-  static constexpr unsigned TX_B = unsigned(bH + bLH + bX + bY + 3 * bO + (kDiag ? 2 * bO : 0));
+  static constexpr unsigned TX_B =
+      unsigned(bH + bLH + bX + bY + bO + (kOwnRing ? 2 * bO : 0) + (kDiag ? 2 * bO : 0));
   static constexpr size_t SLOT = A_END > B_END ? A_END : B_END;
 };
 
@@ -167,8 +171,10 @@ __device__ __forceinline__ void issue(const Ring<S>& rg, const Maps& mp, const S
     tma_load_3d(st + C::B_FX, &mp.fx, bar, x0 - C::H, y0, pz);
     tma_load_3d(st + C::B_FY, &mp.fy, bar, x0, y0 - 1, pz);
     tma_load_3d(st + C::B_FZ, &mp.fz, bar, x0, y0, pz);
-    tma_load_3d(st + C::B_ZO, &mp.zb_o, bar, x0, y0, pz);
-    tma_load_3d(st + C::B_XO, &mp.xh_o, bar, x0, y0, pz);
+    if constexpr (C::kOwnRing) {
+      tma_load_3d(st + C::B_ZO, &mp.zb_o, bar, x0, y0, pz);
+      tma_load_3d(st + C::B_XO, &mp.xh_o, bar, x0, y0, pz);
+    }
     if constexpr (C::kDiag) {
       tma_load_3d(st + C::B_DG, &mp.dg_o, bar, x0, y0, pz);
       tma_load_3d(st + C::B_IDG, &mp.idg_o, bar, x0, y0, pz);
@@ -385,11 +391,14 @@ __device__ bool sweep_tma(const SolveArgs& a, const Maps& mp, const Ring<S>& rg,
         }
         st_cells<T, 4>(pnew, iz, nv, vc);
       } else {
-        const T* ZOc = reinterpret_cast<const T*>(sc + C::B_ZO);
-        const T* XOc = reinterpret_cast<const T*>(sc + C::B_XO);
         T zo[4], xo[4], zn[4], xn[4];
-        ld4s(ZOc + oo, zo);
-        ld4s(XOc + oo, xo);
+        if constexpr (C::kOwnRing) {
+          ld4s(reinterpret_cast<const T*>(sc + C::B_ZO) + oo, zo);
+          ld4s(reinterpret_cast<const T*>(sc + C::B_XO) + oo, xo);
+        } else {
+          ld_cells<T, 4, false>(zbw, iz, nv, zo);
+          ld_cells<T, 4, false>(xhw, iz, nv, xo);
+        }
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
           const T u = vc[c];
@@ -624,7 +633,8 @@ bool tma_eligible(const Geo& g) { return g.nx % 8 == 0 && encode_fn() != nullptr
 
 int launch_solve_tma(sld_system s, SolveArgs& a, const sld_options& o, float* ms, std::string* msg) {
   const bool wacc = a.d <= kWarpAccMaxD;
-  if (a.fp64) return wacc ? launch_tma<double, 8, 3, true>(s, a, o, ms, msg) : launch_tma<double, 8, 3, false>(s, a, o, ms, msg);
+  if (a.fp64)
+    return wacc ? launch_tma<double, 8, 3, true>(s, a, o, ms, msg) : launch_tma<double, 8, 3, false>(s, a, o, ms, msg);
   // FP32 inner: 64 x 16 tiles, 3-deep ring (measured faster than 64 x 8
   // tiles with 4- or 5-deep rings on the 256 x 256 x 128 workload)
   return wacc ? launch_tma<float, 16, 3, true>(s, a, o, ms, msg) : launch_tma<float, 16, 3, false>(s, a, o, ms, msg);
