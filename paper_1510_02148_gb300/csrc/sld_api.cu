@@ -232,6 +232,7 @@ sld_status sld_make_labels(sld_system s, int Sx, int Sy, int Sz, const double* t
   if (!s->label && (e = dalloc(&s->label, s->g.n)) != cudaSuccess) return cuda_fail(e, "alloc labels");
   if ((e = sld::launch_labels(s, Sx, Sy, Sz, htau, L)) != cudaSuccess) return cuda_fail(e, "labels");
   s->have_labels_d = (int)d;
+  s->labels_L = L;
   s->deflation_ready = false;
   if (labels_out) {
     if ((e = cudaMemcpyAsync(labels_out, s->label, sizeof(int32_t) * s->g.n, kind_out(labels_out), s->stream)) !=
@@ -254,6 +255,7 @@ sld_status sld_build_deflation(sld_system s, const int32_t* labels, int d, const
     if (!s->label && (e = dalloc(&s->label, s->g.n)) != cudaSuccess) return cuda_fail(e, "alloc labels");
     if ((e = cudaMemcpyAsync(s->label, labels, sizeof(int32_t) * s->g.n, kind_in(labels), s->stream)) != cudaSuccess)
       return cuda_fail(e, "copy labels");
+    s->labels_L = 0;  // any labels: no subdomain structure assumed
   } else if (!s->label || s->have_labels_d == 0) {
     return fail(SLD_ERR_STATE, "no labels: pass them or call sld_make_labels first");
   }

@@ -43,6 +43,7 @@ struct SolveArgs {
   int d;
   const int32_t* label;
   const uint16_t* label16;  // the same labels as 16-bit (streamed by the TMA sweeps)
+  int lab_L;                // labels are subdomain * lab_L + class (1..4), or 0: any labels
   const double* Einv;     // d x d
   // FP64 operator
   const double *Tx64, *Ty64, *Tz64, *diag64, *invdiag64, *b;
@@ -84,6 +85,7 @@ struct sld_system_s {
   int32_t* label = nullptr;
   uint16_t* label16 = nullptr;
   int d = 0, have_labels_d = 0;
+  int labels_L = 0;  // L of labels made by sld_make_labels (0 after user labels)
   double *E = nullptr, *Einv = nullptr;
   bool deflation_ready = false;
   // solve work space (lazily made)

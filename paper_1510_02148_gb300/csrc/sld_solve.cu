@@ -163,8 +163,8 @@ __device__ void sweep_A(const SolveArgs& a, const Sm<T>& sm, const T* zb, const 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int k = threadIdx.x; k < (WACC ? kTY : 1) * d; k += blockDim.x) sm.acc[k] = 0.0;
   __syncthreads();
-  int cur = -1;
-  T run = T(0);
+  LabelAcc<T, WACC> la;
+  la.init(a.lab_L);
   double dgam = 0.0;
   const int64_t t0 = a.ntiles * blockIdx.x / gridDim.x, t1 = a.ntiles * (blockIdx.x + 1) / gridDim.x;
   for (int64_t t = t0; t < t1;) {
@@ -282,16 +282,8 @@ __device__ void sweep_A(const SolveArgs& a, const Sm<T>& sm, const T* zb, const 
           const T fxm = (c > 0) ? fx[(c > 0) ? c - 1 : 0] : txl;
           const T v = stencil<T>(dxc[c] || dyc || dzc, u, dg[c], fxm, xm, !dxm[c], fx[c], xp, !dxp[c], fym[c],
                                  ym[c], !dym, fy[c], yp[c], !dyp, tzm[c], pm[c], !dzm, fz[c], pn[c], !dzp);
-          const int l = valid ? lb[c] : cur;
-          if (__any_sync(kFull, l != cur)) {
-            warp_flush<WACC>(cur, (double)run, sm.acc, d, warp);
-            cur = l;
-            run = T(0);
-          }
-          if (valid) {
-            run += v;
-            gam += u * v;
-          }
+          la.add(valid, lb[c], v, sm.acc, d, warp);
+          if (valid) gam += u * v;
         }
         st_cells<T, CX>(pnew, iz, sg.nv, pc);
 #pragma unroll
@@ -304,7 +296,7 @@ __device__ void sweep_A(const SolveArgs& a, const Sm<T>& sm, const T* zb, const 
     }
     dgam += (double)gam;
   }
-  if (warp < kTY) warp_flush<WACC>(cur, (double)run, sm.acc, d, warp);
+  if (warp < kTY) la.flush(sm.acc, d, warp);
   const double gsum = block_sum(dgam, sm.red);  // contains __syncthreads
   for (int k = threadIdx.x; k < d; k += blockDim.x) {
     double t = 0.0;
@@ -563,6 +555,10 @@ int run_solve(sld_system s, const double* b_dev, const sld_options& o, sld_resul
   a.d = s->d;
   a.label = s->label;
   a.label16 = s->label16;
+  // labels from the subdomain-levelset rule with d = S * L keep that structure
+  a.lab_L = (s->labels_L >= 1 && s->labels_L <= 4 && s->d == s->have_labels_d) ? s->labels_L : 0;
+  const char* lmode = std::getenv("SLD_LABEL_MODE");  // "general": treat labels as unstructured
+  if (lmode && std::strcmp(lmode, "general") == 0) a.lab_L = 0;
   a.Einv = s->Einv;
   a.Tx64 = s->Tx;
   a.Ty64 = s->Ty;

@@ -58,6 +58,92 @@ __device__ __forceinline__ void warp_flush(int cur, double acc, double* sacc, in
   }
 }
 
+// Per-lane accumulation of v into the label sums s = Z^T v.  Each lane keeps
+// a run sum for its current label; a change of label is a vote of the warp.
+//   L == 0 (labels of any form): every change flushes the runs warp-wide.
+//   1 <= L <= 4 (labels made by the subdomain-levelset rule, label =
+//     subdomain * L + class): a lane whose label changes banks its run in one
+//     of L class slots of its current subdomain, without touching the other
+//     lanes; only a change of some lane's subdomain flushes warp-wide --
+//     rare, since tiles follow the grid and subdomains are boxes of it.
+// A flush groups the lanes with __match_any_sync and sums each group in lane
+// order by its lowest lane, so no two lanes of a warp write one slot.
+template <typename T, bool WACC>
+struct LabelAcc {
+  int L;
+  float invL;
+  int curl;  // current label, -1 = none
+  int curs;  // current subdomain (L > 0), -1 = none
+  T run, a0, a1, a2, a3;
+  __device__ __forceinline__ void init(int L_) {
+    L = L_;
+    invL = L_ > 0 ? 1.0f / (float)L_ : 0.0f;
+    curl = curs = -1;
+    run = a0 = a1 = a2 = a3 = T(0);
+  }
+  __device__ __forceinline__ int sub_of(int lab) const { return __float2int_rz(((float)lab + 0.5f) * invL); }
+  // add the run into the class slot of the current label
+  __device__ __forceinline__ void bank() {
+    if (curl >= 0) {
+      const int cls = curl - curs * L;
+      a0 += (cls == 0) ? run : T(0);
+      a1 += (cls == 1) ? run : T(0);
+      a2 += (cls == 2) ? run : T(0);
+      a3 += (cls == 3) ? run : T(0);
+    }
+    run = T(0);
+  }
+  __device__ __forceinline__ void flush_group(int key, int nk, double* sacc, int d, int warp) {
+    const int lane = threadIdx.x & 31;
+    const unsigned grp = __match_any_sync(kFull, key);
+    for (int k = 0; k < nk; ++k) {
+      const double mine = (double)(L == 0 ? run : (k == 0 ? a0 : k == 1 ? a1 : k == 2 ? a2 : a3));
+      double sum = 0.0;
+#pragma unroll 4
+      for (int src = 0; src < 32; ++src) {
+        const double v = __shfl_sync(kFull, mine, src);
+        if ((grp >> src) & 1u) sum += v;
+      }
+      if (key >= 0 && lane == __ffs(grp) - 1) {
+        const int slot = L > 0 ? key * L + k : key;
+        if constexpr (WACC) sacc[warp * d + slot] += sum;
+        else atomicAdd(&sacc[slot], sum);
+      }
+    }
+  }
+  // everything accumulated so far into the shared sums (warp-wide)
+  __device__ __forceinline__ void flush(double* sacc, int d, int warp) {
+    if (L == 0) {
+      flush_group(curl, 1, sacc, d, warp);
+      run = T(0);
+    } else {
+      bank();
+      flush_group(curs, L, sacc, d, warp);
+      a0 = a1 = a2 = a3 = T(0);
+    }
+  }
+  // one cell; every lane of the warp calls this together
+  __device__ __forceinline__ void add(bool valid, int lab, T v, double* sacc, int d, int warp) {
+    const int l = valid ? lab : curl;
+    if (__any_sync(kFull, l != curl)) {
+      if (L == 0) {
+        flush(sacc, d, warp);
+      } else {
+        const bool ch = l != curl;
+        if (ch) bank();
+        const int ns = ch ? sub_of(l) : curs;
+        if (__any_sync(kFull, ns != curs)) {
+          flush_group(curs, L, sacc, d, warp);
+          a0 = a1 = a2 = a3 = T(0);
+          curs = ns;
+        }
+      }
+      curl = l;
+    }
+    if (valid) run += v;
+  }
+};
+
 // The 7-point operator at one free or Dirichlet cell.
 //   FP32 inner form: sum over faces T (u_i - m_j u_j)  (m_j = 0 for a Dirichlet
 //   neighbour), exact zero row sums, no cancellation of diag * u against the

@@ -216,8 +216,8 @@ __device__ bool sweep_tma(const SolveArgs& a, const Maps& mp, const Ring<S>& rg,
   __syncthreads();
   refill();
   uint64_t item = gitem;
-  int cur = -1;
-  T run = T(0);
+  LabelAcc<T, WACC> la;
+  la.init(a.lab_L);
   T acc1 = T(0), acc2 = T(0);
   double dacc1 = 0.0, dacc2 = 0.0;
   bool ok = true;
@@ -378,16 +378,8 @@ __device__ bool sweep_tma(const SolveArgs& a, const Maps& mp, const Ring<S>& rg,
           const T fxm = (c > 0) ? fx[(c > 0) ? c - 1 : 0] : fxl;
           const T v = stencil<T>(dxc[c] || dyc || dzc, u, dg[c], fxm, xm, !dxm[c], fx[c], xp, !dxp[c], fym[c],
                                  ym[c], !dym, fy[c], yp[c], !dyp, tzm[c], vm[c], !dzm, fz[c], vn[c], !dzp);
-          const int l = valid ? lb[c] : cur;
-          if (__any_sync(kFull, l != cur)) {
-            warp_flush<WACC>(cur, (double)run, sacc, d, warp);
-            cur = l;
-            run = T(0);
-          }
-          if (valid) {
-            run += v;
-            acc1 += u * v;
-          }
+          la.add(valid, lb[c], v, sacc, d, warp);
+          if (valid) acc1 += u * v;
         }
         st_cells<T, 4>(pnew, iz, nv, vc);
       } else {
@@ -450,7 +442,7 @@ __device__ bool sweep_tma(const SolveArgs& a, const Maps& mp, const Ring<S>& rg,
   (void)first;
   fence_proxy_async();  // this sweep's global stores before later TMA reads
   if constexpr (IS_A) {
-    warp_flush<WACC>(cur, (double)run, sacc, d, warp);
+    la.flush(sacc, d, warp);
     const double gsum = block_sum(dacc1, red);
     for (int k = tid; k < d; k += blockDim.x) {
       double s = 0.0;

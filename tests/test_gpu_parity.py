@@ -253,3 +253,25 @@ def test_coarse_singular_reported(sld):
     x, info = s.solve(precision=0)
     assert info.true_relres <= 1.5e-9
     s.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_solve_with_user_labels(sld, oracle_mod, precision):
+    """Labels passed in by the caller (no subdomain structure assumed by the
+    kernels) give the same solve as the oracle."""
+    P = W.lognormal_point_source(64, 48, 40, 8, (4, 3, 4), seed=2)
+    A, lab = _oracle_setup(oracle_mod, P)
+    # scramble the label numbering: same partition, arbitrary ids
+    perm = np.random.default_rng(7).permutation(P.d).astype(np.int32)
+    lab2 = perm[lab]
+    ref = oracle_mod.dpcg(A, lab2, P.d, tol=P.tol)
+    s = sld.System(P.K.reshape(-1).copy(), P.q.reshape(-1).copy(), P.bc_type, P.bc_value, shape=P.shape)
+    s.build_deflation(P.d, labels=lab2)
+    x, info = s.solve(precision=precision)
+    if precision == 0:
+        assert _relerr(x, ref.x) <= 1e-7 and abs(info.iterations - ref.iterations) <= 2
+    else:
+        tight = oracle_mod.dpcg(A, lab2, P.d, tol=1e-13)
+        assert _relerr(x, tight.x) <= max(1e-7, 3 * _relerr(ref.x, tight.x))
+        assert info.true_relres <= 1e-9
+    s.close()
