@@ -59,7 +59,7 @@ __global__ void k_count_bad_K(int64_t n, const double* __restrict__ K, unsigned 
   }
 }
 
-sld_status ensure_workspace(sld_system s, bool need_fp32) {
+sld_status ensure_workspace(sld_system s, bool need_fp32, bool need_bf16) {
   const int64_t n = s->g.n;
   cudaError_t e;
   if (!s->x) {
@@ -89,6 +89,34 @@ sld_status ensure_workspace(sld_system s, bool need_fp32) {
     if ((e = dalloc(&s->Ty32, n)) != cudaSuccess) return cuda_fail(e, "alloc Ty32");
     if ((e = dalloc(&s->Tz32, n)) != cudaSuccess) return cuda_fail(e, "alloc Tz32");
     if ((e = sld::launch_quantize_fp32(s)) != cudaSuccess) return cuda_fail(e, "fp32 coefficients");
+  }
+  if (need_bf16 && !s->bf16_ready) {
+    // BF16 faces, their FP32 inverse diagonal, and E = Z^T A16 Z of the
+    // quantized operator with its inverse (the inner iterations deflate with
+    // the operator they apply)
+    if (!s->Tx16) {
+      if ((e = dalloc(&s->Tx16, n)) != cudaSuccess) return cuda_fail(e, "alloc Tx16");
+      if ((e = dalloc(&s->Ty16, n)) != cudaSuccess) return cuda_fail(e, "alloc Ty16");
+      if ((e = dalloc(&s->Tz16, n)) != cudaSuccess) return cuda_fail(e, "alloc Tz16");
+      if ((e = dalloc(&s->invd16, n)) != cudaSuccess) return cuda_fail(e, "alloc invd16");
+    }
+    dfree(s->E16);
+    dfree(s->Einv16);
+    s->E16 = s->Einv16 = nullptr;
+    if ((e = dalloc(&s->E16, (size_t)s->d * s->d)) != cudaSuccess) return cuda_fail(e, "alloc E16");
+    if ((e = dalloc(&s->Einv16, (size_t)s->d * s->d)) != cudaSuccess) return cuda_fail(e, "alloc Einv16");
+    if ((e = sld::launch_quantize_bf16(s)) != cudaSuccess) return cuda_fail(e, "bf16 coefficients");
+    double* wide = nullptr;
+    if ((e = dalloc(&wide, 3 * (size_t)n)) != cudaSuccess) return cuda_fail(e, "alloc widened faces");
+    int bad = 0;
+    e = sld::launch_widen_bf16(s, wide, wide + n, wide + 2 * n);
+    if (e == cudaSuccess) e = sld::launch_coarse_E(s, wide, wide + n, wide + 2 * n, s->E16, &bad);
+    dfree(wide);
+    if (e != cudaSuccess) return cuda_fail(e, "bf16 coarse matrix");
+    std::string msg;
+    const int st = sld::coarse_factor(s, s->E16, s->Einv16, 2.0, &msg);
+    if (st != SLD_OK) return fail((sld_status)st, "bf16 coarse matrix: " + msg);
+    s->bf16_ready = true;
   }
   return SLD_OK;
 }
@@ -268,13 +296,15 @@ sld_status sld_build_deflation(sld_system s, const int32_t* labels, int d, const
   }
   s->d = d;
   s->deflation_ready = false;
+  s->bf16_ready = false;
   int bad = 0;
-  if ((e = sld::launch_coarse_E(s, &bad)) != cudaSuccess) return cuda_fail(e, "coarse matrix");
+  if ((e = sld::launch_coarse_E(s, s->Tx, s->Ty, s->Tz, s->E, &bad)) != cudaSuccess)
+    return cuda_fail(e, "coarse matrix");
   if (bad) return fail(SLD_ERR_INVALID_ARG, "a label is outside [0, d)");
   if (!s->label16 && (e = dalloc(&s->label16, s->g.n)) != cudaSuccess) return cuda_fail(e, "alloc labels16");
   if ((e = sld::launch_labels16(s)) != cudaSuccess) return cuda_fail(e, "labels16");
   std::string msg;
-  const int st = sld::coarse_factor(s, 2.0, &msg);
+  const int st = sld::coarse_factor(s, s->E, s->Einv, 2.0, &msg);
   if (st != SLD_OK) return fail((sld_status)st, msg);
   s->deflation_ready = true;
   return SLD_OK;
@@ -288,12 +318,12 @@ sld_status sld_solve(sld_system s, const double* b, const sld_options* opt, doub
   sld_options o;
   sld_default_options(&o);
   if (opt) o = *opt;
-  if (o.precision != SLD_FP64 && o.precision != SLD_FP32_IR)
-    return fail(SLD_ERR_INVALID_ARG, "precision must be SLD_FP64 or SLD_FP32_IR");
+  if (o.precision != SLD_FP64 && o.precision != SLD_FP32_IR && o.precision != SLD_BF16COEF_IR)
+    return fail(SLD_ERR_INVALID_ARG, "precision must be SLD_FP64, SLD_FP32_IR or SLD_BF16COEF_IR");
   if (!(o.tol > 0) || !(o.tol < 1)) return fail(SLD_ERR_INVALID_ARG, "tol must be in (0, 1)");
   if (!(o.inner_tol > 0) || !(o.inner_tol < 1)) return fail(SLD_ERR_INVALID_ARG, "inner_tol must be in (0, 1)");
   if (o.maxiter < 1 || o.max_outer < 1) return fail(SLD_ERR_INVALID_ARG, "maxiter and max_outer must be >= 1");
-  sld_status st = ensure_workspace(s, o.precision != SLD_FP64);
+  sld_status st = ensure_workspace(s, o.precision == SLD_FP32_IR, o.precision == SLD_BF16COEF_IR);
   if (st != SLD_OK) return st;
   const int64_t n = s->g.n;
   const double* bd = s->b;
@@ -330,6 +360,7 @@ void sld_destroy(sld_system s) {
   if (!s) return;
   if (s->stream) cudaStreamSynchronize(s->stream);
   void* ptrs[] = {s->K, s->Tx, s->Ty, s->Tz, s->diag, s->invdiag, s->b, s->Tx32, s->Ty32, s->Tz32,
+                  s->Tx16, s->Ty16, s->Tz16, s->invd16, s->E16, s->Einv16,
                   s->label, s->label16, s->E, s->Einv, s->x, s->r64, s->bwork, s->z, s->p0, s->p1, s->xh,
                   s->part, s->s_glob, s->y_glob, s->out, s->bar, s->status};
   for (void* p : ptrs) dfree(p);

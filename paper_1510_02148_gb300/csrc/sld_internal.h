@@ -44,7 +44,9 @@ struct SolveArgs {
   const int32_t* label;
   const uint16_t* label16;  // the same labels as 16-bit (streamed by the TMA sweeps)
   int lab_L;                // labels are subdomain * lab_L + class (1..4), or 0: any labels
-  const double* Einv;     // d x d
+  const double* Einv;     // d x d, E = Z^T A Z of the FP64 operator (refinement steps)
+  const double* Einv_inner;  // the inverse used by the inner iterations (E of their operator)
+  const float* invdi;     // BF16 form: FP32 inverse diagonal of the quantized operator
   // FP64 operator
   const double *Tx64, *Ty64, *Tz64, *diag64, *invdiag64, *b;
   double* x;              // solution (FP64)
@@ -62,6 +64,7 @@ struct SolveArgs {
   double tol, inner_tol;
   int maxiter, max_outer;
   int fp64;               // 1: inner in FP64, single inner solve + finalisation
+  int bf16;               // 1: inner faces stored as BF16
 };
 
 enum {
@@ -81,6 +84,11 @@ struct sld_system_s {
   double *diag = nullptr, *invdiag = nullptr, *b = nullptr;
   // FP32 inner operator (lazily made)
   float *Tx32 = nullptr, *Ty32 = nullptr, *Tz32 = nullptr;
+  // BF16 inner operator, its FP32 inverse diagonal and coarse inverse (lazily made)
+  __nv_bfloat16 *Tx16 = nullptr, *Ty16 = nullptr, *Tz16 = nullptr;
+  float* invd16 = nullptr;
+  double *E16 = nullptr, *Einv16 = nullptr;
+  bool bf16_ready = false;
   // deflation
   int32_t* label = nullptr;
   uint16_t* label16 = nullptr;
@@ -102,8 +110,12 @@ namespace sld {
 // sld_setup.cu
 cudaError_t launch_assemble(sld_system s, const double* q);
 cudaError_t launch_labels(sld_system s, int Sx, int Sy, int Sz, const double* tau, int L);
-cudaError_t launch_coarse_E(sld_system s, int* bad_label);
-int coarse_factor(sld_system s, double timeout_s, std::string* msg);  // returns sld_status
+cudaError_t launch_coarse_E(sld_system s, const double* Tx, const double* Ty, const double* Tz, double* E,
+                            int* bad_label);
+int coarse_factor(sld_system s, const double* E, double* Einv, double timeout_s,
+                  std::string* msg);  // returns sld_status
+cudaError_t launch_quantize_bf16(sld_system s);
+cudaError_t launch_widen_bf16(sld_system s, double* Tx, double* Ty, double* Tz);
 cudaError_t launch_quantize_fp32(sld_system s);
 cudaError_t launch_labels16(sld_system s);
 cudaError_t launch_apply_A(sld_system s, const double* x, double* y);

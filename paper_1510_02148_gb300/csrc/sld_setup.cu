@@ -249,6 +249,40 @@ __global__ void k_convert(int64_t n, const double* __restrict__ a, Tout* __restr
   if (i < n) o[i] = (Tout)a[i];
 }
 
+// BF16 inner operator: each face rounded to nearest BF16, and the FP32
+// inverse of the quantized operator's diagonal (the sum of the six rounded
+// faces, in the order -z, -y, -x, +x, +y, +z, as the sweeps add them), 1 for
+// a Dirichlet cell.  The quantized operator is again a weighted Laplacian with
+// the Dirichlet couplings, so it stays symmetric positive definite.
+__global__ void k_quantize_bf16(Geo g, const double* __restrict__ Tx, const double* __restrict__ Ty,
+                                const double* __restrict__ Tz, __nv_bfloat16* __restrict__ Tx16,
+                                __nv_bfloat16* __restrict__ Ty16, __nv_bfloat16* __restrict__ Tz16,
+                                float* __restrict__ invd) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= g.n) return;
+  const int ix = (int)(i % g.nx), iy = (int)((i / g.nx) % g.ny), iz = (int)(i / g.nxy);
+  auto q = [](double t) { return __double2bfloat16(t); };
+  const __nv_bfloat16 px = q(Tx[i]), py = q(Ty[i]), pz = q(Tz[i]);
+  Tx16[i] = px;
+  Ty16[i] = py;
+  Tz16[i] = pz;
+  if (dir_axis(ix, g.nx, g.dlo_x, g.dhi_x) || dir_axis(iy, g.ny, g.dlo_y, g.dhi_y) ||
+      dir_axis(iz, g.nz, g.dlo_z, g.dhi_z)) {
+    invd[i] = 1.0f;
+    return;
+  }
+  const float mz = iz > 0 ? __bfloat162float(q(Tz[i - g.nxy])) : 0.0f;
+  const float my = iy > 0 ? __bfloat162float(q(Ty[i - g.nx])) : 0.0f;
+  const float mx = ix > 0 ? __bfloat162float(q(Tx[i - 1])) : 0.0f;
+  const float dsum = ((((mz + my) + mx) + __bfloat162float(px)) + __bfloat162float(py)) + __bfloat162float(pz);
+  invd[i] = 1.0f / dsum;
+}
+
+__global__ void k_widen_bf16(int64_t n, const __nv_bfloat16* __restrict__ a, double* __restrict__ o) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) o[i] = (double)__bfloat162float(a[i]);
+}
+
 // 16-bit copy of the labels (d <= 65535), streamed by the TMA sweeps.
 __global__ void k_convert_labels(int64_t n, const int32_t* __restrict__ a, uint16_t* __restrict__ o) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -370,7 +404,8 @@ cudaError_t launch_labels(sld_system s, int Sx, int Sy, int Sz, const double* ta
   return cudaGetLastError();
 }
 
-cudaError_t launch_coarse_E(sld_system s, int* bad_label) {
+cudaError_t launch_coarse_E(sld_system s, const double* Tx, const double* Ty, const double* Tz, double* E,
+                            int* bad_label) {
   const int d = s->d;
   BcVals bc;
   for (int f = 0; f < 6; ++f) {
@@ -383,12 +418,12 @@ cudaError_t launch_coarse_E(sld_system s, int* bad_label) {
   if ((e = cudaMallocAsync(&cnt, sizeof(unsigned long long) * d + sizeof(int) * 4, s->stream)) != cudaSuccess) return e;
   bad = reinterpret_cast<int*>(cnt + d);
   cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * d + sizeof(int) * 4, s->stream);
-  cudaMemsetAsync(s->E, 0, sizeof(double) * d * d, s->stream);
+  cudaMemsetAsync(E, 0, sizeof(double) * d * d, s->stream);
   const size_t smem = sizeof(double) * d + sizeof(unsigned) * d;
   cudaFuncSetAttribute(k_coarse_E, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const unsigned grid = (unsigned)std::min<int64_t>(blocks_for(s->g.n, 256), (int64_t)s->nsm * 4);
-  k_coarse_E<<<grid, 256, smem, s->stream>>>(s->g, bc, d, s->label, s->Tx, s->Ty, s->Tz, s->E, cnt, bad);
-  k_pin_empty<<<blocks_for(d, 128), 128, 0, s->stream>>>(d, cnt, s->E);
+  k_coarse_E<<<grid, 256, smem, s->stream>>>(s->g, bc, d, s->label, Tx, Ty, Tz, E, cnt, bad);
+  k_pin_empty<<<blocks_for(d, 128), 128, 0, s->stream>>>(d, cnt, E);
   int hbad = 0;
   cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
   e = cudaStreamSynchronize(s->stream);
@@ -398,7 +433,7 @@ cudaError_t launch_coarse_E(sld_system s, int* bad_label) {
   return e;
 }
 
-int coarse_factor(sld_system s, double timeout_s, std::string* msg) {
+int coarse_factor(sld_system s, const double* E, double* Einv, double timeout_s, std::string* msg) {
   const int d = s->d;
   double *A = nullptr, *Lm = nullptr, *W = nullptr;
   unsigned* bar = nullptr;
@@ -413,7 +448,7 @@ int coarse_factor(sld_system s, double timeout_s, std::string* msg) {
   W = Lm + (size_t)d * d;
   bar = reinterpret_cast<unsigned*>(W + (size_t)d * d);
   st = reinterpret_cast<int*>(bar + 4);
-  cudaMemcpyAsync(A, s->E, mat, cudaMemcpyDeviceToDevice, s->stream);
+  cudaMemcpyAsync(A, E, mat, cudaMemcpyDeviceToDevice, s->stream);
   cudaMemsetAsync(Lm, 0, mat, s->stream);
   cudaMemsetAsync(bar, 0, 64, s->stream);
   SyncArgs sy{bar, st, (unsigned long long)(timeout_s * 1e9), 0};
@@ -446,7 +481,7 @@ int coarse_factor(sld_system s, double timeout_s, std::string* msg) {
   cudaFuncSetAttribute(k_tri_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
   k_tri_inverse<<<std::max(1, std::min((d + wpb - 1) / wpb, s->nsm * 2)), 32 * wpb, smem2, s->stream>>>(d, Lm, W);
   dim3 tg((d + 15) / 16, (d + 15) / 16);
-  k_wtw<<<tg, dim3(16, 16), 0, s->stream>>>(d, W, s->Einv);
+  k_wtw<<<tg, dim3(16, 16), 0, s->stream>>>(d, W, Einv);
   e = cudaStreamSynchronize(s->stream);
   if (e == cudaSuccess) e = cudaGetLastError();
   cudaFreeAsync(A, s->stream);
@@ -462,6 +497,20 @@ cudaError_t launch_quantize_fp32(sld_system s) {
   k_convert<float><<<blocks_for(n, 256), 256, 0, s->stream>>>(n, s->Tx, s->Tx32);
   k_convert<float><<<blocks_for(n, 256), 256, 0, s->stream>>>(n, s->Ty, s->Ty32);
   k_convert<float><<<blocks_for(n, 256), 256, 0, s->stream>>>(n, s->Tz, s->Tz32);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_quantize_bf16(sld_system s) {
+  k_quantize_bf16<<<blocks_for(s->g.n, 256), 256, 0, s->stream>>>(s->g, s->Tx, s->Ty, s->Tz, s->Tx16, s->Ty16,
+                                                                 s->Tz16, s->invd16);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_widen_bf16(sld_system s, double* Tx, double* Ty, double* Tz) {
+  const int64_t n = s->g.n;
+  k_widen_bf16<<<blocks_for(n, 256), 256, 0, s->stream>>>(n, s->Tx16, Tx);
+  k_widen_bf16<<<blocks_for(n, 256), 256, 0, s->stream>>>(n, s->Ty16, Ty);
+  k_widen_bf16<<<blocks_for(n, 256), 256, 0, s->stream>>>(n, s->Tz16, Tz);
   return cudaGetLastError();
 }
 

@@ -560,6 +560,10 @@ int run_solve(sld_system s, const double* b_dev, const sld_options& o, sld_resul
   const char* lmode = std::getenv("SLD_LABEL_MODE");  // "general": treat labels as unstructured
   if (lmode && std::strcmp(lmode, "general") == 0) a.lab_L = 0;
   a.Einv = s->Einv;
+  const bool bf16 = o.precision == SLD_BF16COEF_IR;
+  a.Einv_inner = bf16 ? s->Einv16 : s->Einv;
+  a.invdi = bf16 ? s->invd16 : nullptr;
+  a.bf16 = bf16 ? 1 : 0;
   a.Tx64 = s->Tx;
   a.Ty64 = s->Ty;
   a.Tz64 = s->Tz;
@@ -572,6 +576,10 @@ int run_solve(sld_system s, const double* b_dev, const sld_options& o, sld_resul
     a.Txi = s->Tx;
     a.Tyi = s->Ty;
     a.Tzi = s->Tz;
+  } else if (bf16) {
+    a.Txi = s->Tx16;
+    a.Tyi = s->Ty16;
+    a.Tzi = s->Tz16;
   } else {
     a.Txi = s->Tx32;
     a.Tyi = s->Ty32;
@@ -605,6 +613,10 @@ int run_solve(sld_system s, const double* b_dev, const sld_options& o, sld_resul
   const bool wacc = s->d <= kWarpAccMaxD;
   const char* force = std::getenv("SLD_SOLVER_PATH");
   const bool use_tma = tma_eligible(s->g) && !(force && std::strcmp(force, "generic") == 0);
+  if (bf16 && !use_tma) {
+    *msg = "BF16 coefficients are streamed by the TMA sweeps only: they need nx % 8 == 0";
+    return SLD_ERR_INVALID_ARG;
+  }
   res->kernel_path = use_tma ? 1 : 0;
   if (use_tma) {
     st = launch_solve_tma(s, a, o, &ms, msg);

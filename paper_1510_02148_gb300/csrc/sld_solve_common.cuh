@@ -255,7 +255,7 @@ __device__ void sweep_O2(const SolveArgs& a, const double* Yd, double* red, doub
     const double AZy = apply64(a, i, ix, iy, iz, [&](int64_t j) { return Yd[__ldg(a.label + j)]; });
     const double rh = a.r64[i] - AZy;
     a.x[i] = a.x[i] + (double)xh[i] + Yd[__ldg(a.label + i)];
-    const T zt = (T)(rh * a.invdiag64[i]);
+    const T zt = (T)(rh * (a.invdi ? (double)a.invdi[i] : a.invdiag64[i]));
     zb[i] = zt;
     xh[i] = T(0);
     p0[i] = T(0);
@@ -289,11 +289,11 @@ __device__ void phase_reduce_s(const SolveArgs& a) {
 }
 
 // y = E^{-1} s, one warp per row.
-__device__ void phase_coarse(const SolveArgs& a) {
+__device__ void phase_coarse(const SolveArgs& a, const double* Einv) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nw = blockDim.x >> 5;
   for (int j = blockIdx.x * nw + warp; j < a.d; j += gridDim.x * nw) {
-    const double* row = a.Einv + (int64_t)j * a.d;
+    const double* row = Einv + (int64_t)j * a.d;
     double t = 0.0;
     for (int k = lane; k < a.d; k += 32) t += __ldg(row + k) * a.s_glob[k];
     t = warp_sum(t);
@@ -353,7 +353,7 @@ __device__ void solve_body(const SolveArgs& a, double* acc, double* Yd, T* Y, do
     if (!grid_barrier(a.sy, epoch)) { failed = true; break; }
     phase_reduce_s(a);
     if (!grid_barrier(a.sy, epoch)) { failed = true; break; }
-    phase_coarse(a);
+    phase_coarse(a, a.Einv);
     if (!grid_barrier(a.sy, epoch)) { failed = true; break; }
     if (outer == 0) bb = cta_scalar(a, 3, red);
     for (int k = threadIdx.x; k < a.d; k += blockDim.x) Yd[k] = a.y_glob[k];
@@ -381,7 +381,7 @@ __device__ void solve_body(const SolveArgs& a, double* acc, double* Yd, T* Y, do
       if (!grid_barrier(a.sy, epoch)) { failed = true; break; }
       phase_reduce_s(a);
       if (!grid_barrier(a.sy, epoch)) { failed = true; break; }
-      phase_coarse(a);
+      phase_coarse(a, a.Einv_inner);
       if (!grid_barrier(a.sy, epoch)) { failed = true; break; }
       const double gamma = cta_scalar(a, 0, red);
       const double delta = gamma - cta_sdoty(a, red);

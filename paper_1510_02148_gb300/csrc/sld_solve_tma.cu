@@ -29,36 +29,42 @@ namespace {
 
 constexpr int kTX = 64;  // cells per tile row
 
-template <typename T, int TY>
+// T: vector type (double, or float for the inner iteration of the mixed
+// solve); F: stored face type (T, or bf16 for the BF16-coefficient form).
+template <typename T, typename F, int TY>
 struct TCfg {
-  static constexpr int NT = 16 * TY;             // 16 threads per row, 4 cells each
   static constexpr int H = 16 / (int)sizeof(T);  // x halo so that boxes start on 16 bytes
+  static constexpr int HF = 16 / (int)sizeof(F);  // the same for the Fx box
+  static constexpr int WF = kTX + 2 * HF;
   static constexpr int HL = 8;                   // x halo of the (16-bit) label box
   static constexpr int WH = kTX + 2 * H;         // halo box width
   static constexpr int WL = kTX + 2 * HL;
   static constexpr bool kDiag = sizeof(T) == 8;  // FP64 form uses the stored diagonal and inverse
+  static constexpr bool kScale = sizeof(F) == 2;  // BF16 form: FP32 per-cell inverse diagonal
   static constexpr size_t al(size_t b) { return (b + 127) / 128 * 128; }
   static constexpr size_t bH = sizeof(T) * (TY + 2) * WH;   // vector with halo
-  static constexpr size_t bX = sizeof(T) * TY * WH;         // Fx with the face left of the tile
-  static constexpr size_t bY = sizeof(T) * (TY + 1) * kTX;  // Fy with the face below the tile
+  static constexpr size_t bX = sizeof(F) * TY * WF;         // Fx with the face left of the tile
+  static constexpr size_t bY = sizeof(F) * (TY + 1) * kTX;  // Fy with the face below the tile
+  static constexpr size_t bOF = sizeof(F) * TY * kTX;       // Fz, own cells
   static constexpr size_t bO = sizeof(T) * TY * kTX;        // own cells
+  static constexpr size_t bOS = 4 * TY * kTX;               // FP32 per-cell scale, own cells
   static constexpr size_t bLO = 2 * TY * kTX;               // labels, own cells
   static constexpr size_t bLH = 2 * (TY + 2) * WL;          // labels with halo
   // sweep A slot: z(h) p_old(h) Fx Fy Fz labels [diag]
   static constexpr size_t A_ZB = 0, A_PO = al(bH), A_FX = A_PO + al(bH), A_FY = A_FX + al(bX),
-                          A_FZ = A_FY + al(bY), A_LB = A_FZ + al(bO), A_DG = A_LB + al(bLO),
+                          A_FZ = A_FY + al(bY), A_LB = A_FZ + al(bOF), A_DG = A_LB + al(bLO),
                           A_END = A_DG + (kDiag ? al(bO) : 0);
-  static constexpr unsigned TX_A = unsigned(2 * bH + bX + bY + bO + bLO + (kDiag ? bO : 0));
+  static constexpr unsigned TX_A = unsigned(2 * bH + bX + bY + bOF + bLO + (kDiag ? bO : 0));
   // sweep B slot: p(h) labels(h) Fx Fy Fz z xhat [diag, 1/diag].  In the FP64
   // form the own z and xhat are read straight from global memory instead, so
   // that three slots of the wider FP64 boxes fit two CTAs per SM.
   static constexpr bool kOwnRing = !kDiag;  // own z, xhat through the ring
   static constexpr size_t B_P = 0, B_LB = al(bH), B_FX = B_LB + al(bLH), B_FY = B_FX + al(bX),
-                          B_FZ = B_FY + al(bY), B_ZO = B_FZ + al(bO), B_XO = B_ZO + (kOwnRing ? al(bO) : 0),
+                          B_FZ = B_FY + al(bY), B_ZO = B_FZ + al(bOF), B_XO = B_ZO + (kOwnRing ? al(bO) : 0),
                           B_DG = B_XO + (kOwnRing ? al(bO) : 0), B_IDG = B_DG + (kDiag ? al(bO) : 0),
-                          B_END = B_IDG + (kDiag ? al(bO) : 0);
-  static constexpr unsigned TX_B =
-      unsigned(bH + bLH + bX + bY + bO + (kOwnRing ? 2 * bO : 0) + (kDiag ? 2 * bO : 0));
+                          B_SC = B_IDG + (kDiag ? al(bO) : 0), B_END = B_SC + (kScale ? al(bOS) : 0);
+  static constexpr unsigned TX_B = unsigned(bH + bLH + bX + bY + bOF + (kOwnRing ? 2 * bO : 0) +
+                                            (kDiag ? 2 * bO : 0) + (kScale ? bOS : 0));
   static constexpr size_t SLOT = A_END > B_END ? A_END : B_END;
 };
 
@@ -66,7 +72,7 @@ struct TCfg {
 struct Maps {
   CUtensorMap zb_h;     // z with halo          box (WH, TY+2)
   CUtensorMap p_h[2];   // p buffers with halo  box (WH, TY+2)
-  CUtensorMap fx;       // Fx                   box (WH, TY)
+  CUtensorMap fx;       // Fx                   box (WF, TY)
   CUtensorMap fy;       // Fy                   box (kTX, TY+1)
   CUtensorMap fz;       // Fz                   box (kTX, TY)
   CUtensorMap lb_o;     // labels               box (kTX, TY)
@@ -75,6 +81,7 @@ struct Maps {
   CUtensorMap xh_o;     // xhat                 box (kTX, TY)
   CUtensorMap dg_o;     // diag (FP64 form)     box (kTX, TY)
   CUtensorMap idg_o;    // 1/diag (FP64 form)   box (kTX, TY)
+  CUtensorMap sc_o;     // FP32 1/diag (BF16)   box (kTX, TY)
 };
 
 // The CTA's sequence of planes to load: for every segment (column tile ct,
@@ -117,6 +124,21 @@ __device__ __forceinline__ void ld4s(const T* p, T (&v)[4]) {
     v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
   }
 }
+
+// Four stored faces (F = T, or bf16 widened exactly to float).
+template <typename F, typename T>
+__device__ __forceinline__ void ld4f(const F* p, T (&v)[4]) {
+  if constexpr (sizeof(F) == 2) {
+    const uint2 q = *reinterpret_cast<const uint2*>(p);
+    v[0] = __uint_as_float(q.x << 16);
+    v[1] = __uint_as_float(q.x & 0xffff0000u);
+    v[2] = __uint_as_float(q.y << 16);
+    v[3] = __uint_as_float(q.y & 0xffff0000u);
+  } else {
+    ld4s(reinterpret_cast<const T*>(p), v);
+  }
+}
+
 __device__ __forceinline__ void ld4i(const uint16_t* p, int (&v)[4]) {
   const uint2 q = *reinterpret_cast<const uint2*>(p);
   v[0] = (int)(q.x & 0xffffu); v[1] = (int)(q.x >> 16); v[2] = (int)(q.y & 0xffffu); v[3] = (int)(q.y >> 16);
@@ -148,10 +170,10 @@ __device__ void ring_drain(const Ring<S>& rg, const SyncArgs& sy, uint64_t from,
   __syncthreads();
 }
 
-template <typename T, int TY, int S, bool IS_A>
+template <typename T, typename F, int TY, int S, bool IS_A>
 __device__ __forceinline__ void issue(const Ring<S>& rg, const Maps& mp, const SolveArgs& a, int ntx, uint64_t item,
                                       int64_t ct, int pz, int pbuf) {
-  using C = TCfg<T, TY>;
+  using C = TCfg<T, F, TY>;
   unsigned char* st = rg.slot(item);
   uint64_t* bar = rg.full + (item % S);
   const int x0 = (int)(ct % ntx) * kTX, y0 = (int)(ct / ntx) * TY;
@@ -159,7 +181,7 @@ __device__ __forceinline__ void issue(const Ring<S>& rg, const Maps& mp, const S
     mbar_expect_tx(bar, C::TX_A);
     tma_load_3d(st + C::A_ZB, &mp.zb_h, bar, x0 - C::H, y0 - 1, pz);
     tma_load_3d(st + C::A_PO, &mp.p_h[pbuf], bar, x0 - C::H, y0 - 1, pz);
-    tma_load_3d(st + C::A_FX, &mp.fx, bar, x0 - C::H, y0, pz);
+    tma_load_3d(st + C::A_FX, &mp.fx, bar, x0 - C::HF, y0, pz);
     tma_load_3d(st + C::A_FY, &mp.fy, bar, x0, y0 - 1, pz);
     tma_load_3d(st + C::A_FZ, &mp.fz, bar, x0, y0, pz);
     tma_load_3d(st + C::A_LB, &mp.lb_o, bar, x0, y0, pz);
@@ -168,7 +190,7 @@ __device__ __forceinline__ void issue(const Ring<S>& rg, const Maps& mp, const S
     mbar_expect_tx(bar, C::TX_B);
     tma_load_3d(st + C::B_P, &mp.p_h[pbuf], bar, x0 - C::H, y0 - 1, pz);
     tma_load_3d(st + C::B_LB, &mp.lb_h, bar, x0 - C::HL, y0 - 1, pz);
-    tma_load_3d(st + C::B_FX, &mp.fx, bar, x0 - C::H, y0, pz);
+    tma_load_3d(st + C::B_FX, &mp.fx, bar, x0 - C::HF, y0, pz);
     tma_load_3d(st + C::B_FY, &mp.fy, bar, x0, y0 - 1, pz);
     tma_load_3d(st + C::B_FZ, &mp.fz, bar, x0, y0, pz);
     if constexpr (C::kOwnRing) {
@@ -179,15 +201,16 @@ __device__ __forceinline__ void issue(const Ring<S>& rg, const Maps& mp, const S
       tma_load_3d(st + C::B_DG, &mp.dg_o, bar, x0, y0, pz);
       tma_load_3d(st + C::B_IDG, &mp.idg_o, bar, x0, y0, pz);
     }
+    if constexpr (C::kScale) tma_load_3d(st + C::B_SC, &mp.sc_o, bar, x0, y0, pz);
   }
 }
 
 // One sweep (A or B) over the CTA's plane tiles.  `gitem` is the CTA's running
 // item count (identical in all threads), continued across sweeps.
-template <typename T, int TY, int S, bool WACC, bool IS_A>
+template <typename T, typename F, int TY, int S, bool WACC, bool IS_A>
 __device__ bool sweep_tma(const SolveArgs& a, const Maps& mp, const Ring<S>& rg, uint64_t& gitem, int ntx,
                           double* sacc, const T* Y, double* red, int pbuf, T* pnew, T coef, double* part_row) {
-  using C = TCfg<T, TY>;
+  using C = TCfg<T, F, TY>;
   const Geo& g = a.g;
   const int d = a.d;
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -206,7 +229,7 @@ __device__ bool sweep_tma(const SolveArgs& a, const Maps& mp, const Ring<S>& rg,
     if (tid == 0) {
       fence_proxy_async();
       while (pw.more() && issued < released + S) {
-        issue<T, TY, S, IS_A>(rg, mp, a, ntx, issued, pw.ct, pw.plane(), pbuf);
+        issue<T, F, TY, S, IS_A>(rg, mp, a, ntx, issued, pw.ct, pw.plane(), pbuf);
         ++issued;
         pw.next();
       }
@@ -224,7 +247,7 @@ __device__ bool sweep_tma(const SolveArgs& a, const Maps& mp, const Ring<S>& rg,
   // offsets of this thread's cells in the boxes
   const int hi = (r + 1) * C::WH + C::H + 4 * c4;   // vector halo box
   const int hl = (r + 1) * C::WL + C::HL + 4 * c4;  // label halo box
-  const int ox = r * C::WH + C::H + 4 * c4;         // Fx box
+  const int ox = r * C::WF + C::HF + 4 * c4;        // Fx box
   const int oy = (r + 1) * kTX + 4 * c4;            // Fy box (own row)
   const int oo = r * kTX + 4 * c4;                  // own boxes
   for (int64_t t = t0; t < t1;) {
@@ -257,7 +280,7 @@ __device__ bool sweep_tma(const SolveArgs& a, const Maps& mp, const Ring<S>& rg,
         ld4s(reinterpret_cast<const T*>(st + C::A_PO) + hi, po);
 #pragma unroll
         for (int c = 0; c < 4; ++c) vm[c] = zv[c] + coef * po[c];
-        ld4s(reinterpret_cast<const T*>(st + C::A_FZ) + oo, tzm);
+        ld4f(reinterpret_cast<const F*>(st + C::A_FZ) + oo, tzm);
       } else {
         T pv[4];
         int lb[4];
@@ -265,7 +288,7 @@ __device__ bool sweep_tma(const SolveArgs& a, const Maps& mp, const Ring<S>& rg,
         ld4i(reinterpret_cast<const uint16_t*>(st + C::B_LB) + hl, lb);
 #pragma unroll
         for (int c = 0; c < 4; ++c) vm[c] = pv[c] - Y[lb[c]];
-        ld4s(reinterpret_cast<const T*>(st + C::B_FZ) + oo, tzm);
+        ld4f(reinterpret_cast<const F*>(st + C::B_FZ) + oo, tzm);
       }
     }
     if (!__syncthreads_and(ok)) { ring_drain(rg, a.sy, released, issued); return false; }
@@ -322,11 +345,11 @@ __device__ bool sweep_tma(const SolveArgs& a, const Maps& mp, const Ring<S>& rg,
         }
         left = ZBc[hi - 1] + coef * POc[hi - 1];
         right = ZBc[hi + 4] + coef * POc[hi + 4];
-        ld4s(reinterpret_cast<const T*>(sc + C::A_FX) + ox, fx);
-        fxl = reinterpret_cast<const T*>(sc + C::A_FX)[ox - 1];
-        ld4s(reinterpret_cast<const T*>(sc + C::A_FY) + oy, fy);
-        ld4s(reinterpret_cast<const T*>(sc + C::A_FY) + oy - kTX, fym);
-        ld4s(reinterpret_cast<const T*>(sc + C::A_FZ) + oo, fz);
+        ld4f(reinterpret_cast<const F*>(sc + C::A_FX) + ox, fx);
+        fxl = (T)reinterpret_cast<const F*>(sc + C::A_FX)[ox - 1];
+        ld4f(reinterpret_cast<const F*>(sc + C::A_FY) + oy, fy);
+        ld4f(reinterpret_cast<const F*>(sc + C::A_FY) + oy - kTX, fym);
+        ld4f(reinterpret_cast<const F*>(sc + C::A_FZ) + oo, fz);
         ld4i(reinterpret_cast<const uint16_t*>(sc + C::A_LB) + oo, lb);
         if constexpr (C::kDiag) ld4s(reinterpret_cast<const T*>(sc + C::A_DG) + oo, dg);
       } else {
@@ -354,11 +377,11 @@ __device__ bool sweep_tma(const SolveArgs& a, const Maps& mp, const Ring<S>& rg,
         }
         left = Pc[hi - 1] - Y[Lc[hl - 1]];
         right = Pc[hi + 4] - Y[Lc[hl + 4]];
-        ld4s(reinterpret_cast<const T*>(sc + C::B_FX) + ox, fx);
-        fxl = reinterpret_cast<const T*>(sc + C::B_FX)[ox - 1];
-        ld4s(reinterpret_cast<const T*>(sc + C::B_FY) + oy, fy);
-        ld4s(reinterpret_cast<const T*>(sc + C::B_FY) + oy - kTX, fym);
-        ld4s(reinterpret_cast<const T*>(sc + C::B_FZ) + oo, fz);
+        ld4f(reinterpret_cast<const F*>(sc + C::B_FX) + ox, fx);
+        fxl = (T)reinterpret_cast<const F*>(sc + C::B_FX)[ox - 1];
+        ld4f(reinterpret_cast<const F*>(sc + C::B_FY) + oy, fy);
+        ld4f(reinterpret_cast<const F*>(sc + C::B_FY) + oy - kTX, fym);
+        ld4f(reinterpret_cast<const F*>(sc + C::B_FZ) + oo, fz);
         if constexpr (C::kDiag) {
           ld4s(reinterpret_cast<const T*>(sc + C::B_DG) + oo, dg);
           ld4s(reinterpret_cast<const T*>(sc + C::B_IDG) + oo, idg);
@@ -383,7 +406,8 @@ __device__ bool sweep_tma(const SolveArgs& a, const Maps& mp, const Ring<S>& rg,
         }
         st_cells<T, 4>(pnew, iz, nv, vc);
       } else {
-        T zo[4], xo[4], zn[4], xn[4];
+        T zo[4], xo[4], zn[4], xn[4], sci[4] = {};
+        if constexpr (C::kScale) ld4s(reinterpret_cast<const T*>(sc + C::B_SC) + oo, sci);
         if constexpr (C::kOwnRing) {
           ld4s(reinterpret_cast<const T*>(sc + C::B_ZO) + oo, zo);
           ld4s(reinterpret_cast<const T*>(sc + C::B_XO) + oo, xo);
@@ -406,6 +430,7 @@ __device__ bool sweep_tma(const SolveArgs& a, const Maps& mp, const Ring<S>& rg,
           const T rr = dgi * zo[c] - coef * w;
           T znew;
           if constexpr (C::kDiag) znew = rr * idg[c];
+          else if constexpr (C::kScale) znew = rr * sci[c];  // FP32 per-cell inverse diagonal
           else znew = __fdividef(rr, dgi);  // FP32 inner: 2-ulp division
           zn[c] = znew;
           xn[c] = xo[c] + coef * pcur[c];
@@ -465,9 +490,9 @@ __device__ bool sweep_tma(const SolveArgs& a, const Maps& mp, const Ring<S>& rg,
   return true;
 }
 
-template <typename T, int TY, int S, bool WACC>
+template <typename T, typename F, int TY, int S, bool WACC>
 __host__ __device__ constexpr size_t tma_smem_bytes(int d) {
-  using C = TCfg<T, TY>;
+  using C = TCfg<T, F, TY>;
   size_t b = C::SLOT * S;
   b += 8 * S;
   b = (b + 15) / 16 * 16;
@@ -479,9 +504,9 @@ __host__ __device__ constexpr size_t tma_smem_bytes(int d) {
   return b;
 }
 
-template <typename T, int TY, int S, bool WACC>
+template <typename T, typename F, int TY, int S, bool WACC>
 __global__ void __launch_bounds__(16 * TY) k_solve_tma(SolveArgs a, const __grid_constant__ Maps mp, int ntx) {
-  using C = TCfg<T, TY>;
+  using C = TCfg<T, F, TY>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   Ring<S> rg;
   rg.slots = smem_raw;
@@ -509,10 +534,10 @@ __global__ void __launch_bounds__(16 * TY) k_solve_tma(SolveArgs a, const __grid
   solve_body<T, WACC>(
       a, acc, Yd, Y, red,
       [&](int po, T beta, double* part) {
-        return sweep_tma<T, TY, S, WACC, true>(a, mp, rg, gitem, ntx, acc, Y, red, po, pb[po ^ 1], beta, part);
+        return sweep_tma<T, F, TY, S, WACC, true>(a, mp, rg, gitem, ntx, acc, Y, red, po, pb[po ^ 1], beta, part);
       },
       [&](int pn, T alpha, double* part) {
-        return sweep_tma<T, TY, S, WACC, false>(a, mp, rg, gitem, ntx, acc, Y, red, pn, nullptr, alpha, part);
+        return sweep_tma<T, F, TY, S, WACC, false>(a, mp, rg, gitem, ntx, acc, Y, red, pn, nullptr, alpha, part);
       });
 }
 
@@ -543,19 +568,20 @@ bool make_map(CUtensorMap* m, CUtensorMapDataType dt, size_t es, const void* ptr
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <typename T, int TY>
+template <typename T, typename F, int TY>
 bool build_maps(const SolveArgs& a, Maps* mp) {
-  using C = TCfg<T, TY>;
+  using C = TCfg<T, F, TY>;
   const CUtensorMapDataType dt = sizeof(T) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-  const size_t es = sizeof(T);
+  const CUtensorMapDataType df = sizeof(F) == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : dt;
+  const size_t es = sizeof(T), ef = sizeof(F);
   const Geo& g = a.g;
   bool ok = true;
   ok = ok && make_map(&mp->zb_h, dt, es, a.z, g, C::WH, TY + 2);
   ok = ok && make_map(&mp->p_h[0], dt, es, a.p0, g, C::WH, TY + 2);
   ok = ok && make_map(&mp->p_h[1], dt, es, a.p1, g, C::WH, TY + 2);
-  ok = ok && make_map(&mp->fx, dt, es, a.Txi, g, C::WH, TY);
-  ok = ok && make_map(&mp->fy, dt, es, a.Tyi, g, kTX, TY + 1);
-  ok = ok && make_map(&mp->fz, dt, es, a.Tzi, g, kTX, TY);
+  ok = ok && make_map(&mp->fx, df, ef, a.Txi, g, C::WF, TY);
+  ok = ok && make_map(&mp->fy, df, ef, a.Tyi, g, kTX, TY + 1);
+  ok = ok && make_map(&mp->fz, df, ef, a.Tzi, g, kTX, TY);
   ok = ok && make_map(&mp->lb_o, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, a.label16, g, kTX, TY);
   ok = ok && make_map(&mp->lb_h, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, a.label16, g, C::WL, TY + 2);
   ok = ok && make_map(&mp->zb_o, dt, es, a.z, g, kTX, TY);
@@ -564,16 +590,18 @@ bool build_maps(const SolveArgs& a, Maps* mp) {
     ok = ok && make_map(&mp->dg_o, dt, es, a.diag64, g, kTX, TY);
     ok = ok && make_map(&mp->idg_o, dt, es, a.invdiag64, g, kTX, TY);
   } else {
-    mp->dg_o = mp->fz;
-    mp->idg_o = mp->fz;
+    mp->dg_o = mp->zb_o;
+    mp->idg_o = mp->zb_o;
   }
+  if (C::kScale) ok = ok && make_map(&mp->sc_o, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, a.invdi, g, kTX, TY);
+  else mp->sc_o = mp->zb_o;
   return ok;
 }
 
-template <typename T, int TY, int S, bool WACC>
+template <typename T, typename F, int TY, int S, bool WACC>
 int launch_tma(sld_system s, SolveArgs& a, const sld_options& o, float* ms, std::string* msg) {
   Maps mp;
-  if (!build_maps<T, TY>(a, &mp)) {
+  if (!build_maps<T, F, TY>(a, &mp)) {
     *msg = "tensor map creation failed";
     return SLD_ERR_CUDA;
   }
@@ -582,8 +610,8 @@ int launch_tma(sld_system s, SolveArgs& a, const sld_options& o, float* ms, std:
   a.ntiles = (int64_t)ntx * nty * a.g.nz;
   a.ntx = ntx;
   a.nty = nty;
-  const size_t smem = tma_smem_bytes<T, TY, S, WACC>(a.d);
-  auto kern = k_solve_tma<T, TY, S, WACC>;
+  const size_t smem = tma_smem_bytes<T, F, TY, S, WACC>(a.d);
+  auto kern = k_solve_tma<T, F, TY, S, WACC>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) {
     *msg = std::string("tma kernel attribute: ") + cudaGetErrorString(e);
@@ -626,10 +654,15 @@ bool tma_eligible(const Geo& g) { return g.nx % 8 == 0 && encode_fn() != nullptr
 int launch_solve_tma(sld_system s, SolveArgs& a, const sld_options& o, float* ms, std::string* msg) {
   const bool wacc = a.d <= kWarpAccMaxD;
   if (a.fp64)
-    return wacc ? launch_tma<double, 8, 3, true>(s, a, o, ms, msg) : launch_tma<double, 8, 3, false>(s, a, o, ms, msg);
+    return wacc ? launch_tma<double, double, 8, 3, true>(s, a, o, ms, msg)
+                : launch_tma<double, double, 8, 3, false>(s, a, o, ms, msg);
+  if (a.bf16)
+    return wacc ? launch_tma<float, __nv_bfloat16, 16, 3, true>(s, a, o, ms, msg)
+                : launch_tma<float, __nv_bfloat16, 16, 3, false>(s, a, o, ms, msg);
   // FP32 inner: 64 x 16 tiles, 3-deep ring (measured faster than 64 x 8
   // tiles with 4- or 5-deep rings on the 256 x 256 x 128 workload)
-  return wacc ? launch_tma<float, 16, 3, true>(s, a, o, ms, msg) : launch_tma<float, 16, 3, false>(s, a, o, ms, msg);
+  return wacc ? launch_tma<float, float, 16, 3, true>(s, a, o, ms, msg)
+              : launch_tma<float, float, 16, 3, false>(s, a, o, ms, msg);
 }
 
 }  // namespace sld
