@@ -101,7 +101,8 @@ typedef struct {
   double true_relres;      /* ||b - A x||_2 / ||b||_2, recomputed in FP64 after the solve */
   double recursive_relres; /* the iteration's own deflated residual at exit, / ||b|| */
   double solve_ms;         /* device time of the persistent solve kernel (CUDA events) */
-  int kernel_path;         /* 1: TMA-pipelined sweeps (nx % 8 == 0), 0: register/shuffle sweeps */
+  int kernel_path;         /* 1: TMA-pipelined sweeps (nx % 8 == 0), 0: register/shuffle sweeps,
+                              2: batched launch (register/shuffle sweeps) */
 } sld_result;
 
 /* Fill *o with the defaults listed above. */
@@ -167,6 +168,50 @@ sld_status sld_solve(sld_system s, const double* b, const sld_options* o, double
 
 /* Release the handle and its device memory.  NULL is ignored. */
 void sld_destroy(sld_system s);
+
+/* ---------------------------------------------------------------------- */
+/* Batched solves: many independent systems in one persistent launch.     */
+/* ---------------------------------------------------------------------- */
+
+typedef struct sld_batch_s* sld_batch; /* opaque plan; does not own the systems */
+
+/*
+ * Plan a batched solve of `count` systems (each built up to
+ * sld_build_deflation, all on one device; the stream of systems[0] is used).
+ * Every system gets its own team of CTAs in one cooperative launch -- a
+ * share proportional to n^e with e in {1, 4/3} -- with its own barriers and
+ * reductions; teams never wait on each other and leave as soon as their
+ * system is solved.  The launch and the resets of every system's state are
+ * captured in one CUDA graph.  With o->ctas_per_sm == 0 the plan is tuned:
+ * each candidate launch shape (team exponent, cells per lane) solves the
+ * batch once with the assembled right-hand sides and the fastest is kept
+ * (sld_batch_describe lists them).  This is the parallel subdomain idea of
+ * Section 3.2.2 applied across systems: independent problems share the GPU.
+ *   o: SLD_FP64 or SLD_FP32_IR; NULL = defaults.
+ * Errors: SLD_ERR_INVALID_ARG (count > co-resident CTAs, mixed devices,
+ * a system twice), SLD_ERR_STATE (no deflation), SLD_ERR_CUDA.
+ */
+sld_status sld_batch_create(sld_system* systems, int count, const sld_options* o, sld_batch* out);
+
+/*
+ * Run the plan: b[k] (n_k values, host or device; b or b[k] NULL = the
+ * assembled right-hand side) -> x[k] (n_k values, host or device; x or x[k]
+ * may be NULL).  res (count entries, may be NULL) gets each system's
+ * iterations, refinement steps and FP64 true residual; solve_ms is the time
+ * of the whole batched launch; kernel_path = 2.  Returns the first failing
+ * system's status (the others are still solved and reported).
+ */
+sld_status sld_batch_solve(sld_batch bt, const double* const* b, double* const* x, sld_result* res);
+
+/* Text description of the plan (CTAs, teams, tuning times). */
+const char* sld_batch_describe(sld_batch bt);
+
+/* Release the plan (not the systems).  NULL is ignored. */
+void sld_batch_destroy(sld_batch bt);
+
+/* sld_batch_create + sld_batch_solve + sld_batch_destroy. */
+sld_status sld_solve_batched(sld_system* systems, int count, const double* const* b, const sld_options* o,
+                             double* const* x, sld_result* res);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* sld_last_error(void);

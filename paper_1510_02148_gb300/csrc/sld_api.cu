@@ -8,8 +8,18 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "sld_internal.h"
+
+struct sld_batch_s {
+  std::vector<sld_system> sys;
+  sld_options o{};
+  sld::BatchPlan plan;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaStream_t stream = nullptr;  // owned: graph capture and launch
+  std::string desc;
+};
 
 namespace {
 
@@ -439,6 +449,198 @@ sld_status sld_get_coarse(sld_system s, double* E, double* Einv) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) return cuda_fail(e, "copy coarse");
   return SLD_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Results of system s after a solve that ended without a CUDA error.
+sld_status collect(sld_system s, const double* b_dev, double ms, double* x, sld_result* r) {
+  double out[sld::kOutCount];
+  int dev_status = 0;
+  cudaMemcpyAsync(out, s->out, sizeof(out), cudaMemcpyDeviceToHost, s->stream);
+  cudaMemcpyAsync(&dev_status, s->status, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
+  cudaError_t e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "batch readback");
+  r->iterations = (int)out[sld::kOutIters];
+  r->outer_steps = (int)out[sld::kOutOuter];
+  r->recursive_relres = out[sld::kOutBB] > 0 ? std::sqrt(out[sld::kOutRecRR] / out[sld::kOutBB]) : 0.0;
+  r->solve_ms = ms;
+  r->kernel_path = 2;
+  if (dev_status != 0) return fail((sld_status)dev_status, "a device-side wait timed out (team barrier)");
+  double rr = 0, bb = 0;
+  if ((e = sld::launch_residual(s, b_dev, s->x, s->part, &rr, &bb)) != cudaSuccess) return cuda_fail(e, "residual");
+  r->true_relres = bb > 0 ? std::sqrt(rr / bb) : 0.0;
+  if (x) {
+    if ((e = cudaMemcpyAsync(x, s->x, sizeof(double) * s->g.n, kind_out(x), s->stream)) != cudaSuccess)
+      return cuda_fail(e, "copy x out");
+    if ((e = cudaStreamSynchronize(s->stream)) != cudaSuccess) return cuda_fail(e, "copy x out");
+  }
+  const int code = (int)out[sld::kOutStatus];
+  if (code == SLD_ERR_NOT_CONVERGED) return fail(SLD_ERR_NOT_CONVERGED, "not converged within maxiter / max_outer");
+  if (code == SLD_ERR_BREAKDOWN) return fail(SLD_ERR_BREAKDOWN, "breakdown in the deflated iteration");
+  if (code < 0) return fail(SLD_ERR_CUDA, "device error");
+  return SLD_OK;
+}
+
+sld_status batch_launch(sld_batch bt, float* ms) {
+  cudaEventRecord(bt->ev0, bt->stream);
+  cudaError_t e = cudaGraphLaunch(bt->plan.exec, bt->stream);
+  cudaEventRecord(bt->ev1, bt->stream);
+  if (e == cudaSuccess) e = cudaEventSynchronize(bt->ev1);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "batch graph launch");
+  cudaEventElapsedTime(ms, bt->ev0, bt->ev1);
+  return SLD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sld_status sld_batch_create(sld_system* systems, int count, const sld_options* opt, sld_batch* out) {
+  g_last_error.clear();
+  if (!out) return fail(SLD_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!systems || count < 1 || count > 4096) return fail(SLD_ERR_INVALID_ARG, "count must be in [1, 4096]");
+  sld_options o;
+  sld_default_options(&o);
+  if (opt) o = *opt;
+  if (o.precision != SLD_FP64 && o.precision != SLD_FP32_IR)
+    return fail(SLD_ERR_INVALID_ARG, "batched solves take SLD_FP64 or SLD_FP32_IR");
+  if (!(o.tol > 0) || !(o.tol < 1) || !(o.inner_tol > 0) || !(o.inner_tol < 1) || o.maxiter < 1 || o.max_outer < 1)
+    return fail(SLD_ERR_INVALID_ARG, "bad tolerances or iteration caps");
+  for (int k = 0; k < count; ++k) {
+    sld_system s = systems[k];
+    if (!s) return fail(SLD_ERR_INVALID_ARG, "a system is NULL");
+    if (!s->deflation_ready) return fail(SLD_ERR_STATE, "every system needs sld_build_deflation first");
+    if (s->device != systems[0]->device) return fail(SLD_ERR_INVALID_ARG, "systems on different devices");
+    for (int j = 0; j < k; ++j)
+      if (systems[j] == s) return fail(SLD_ERR_INVALID_ARG, "a system appears twice");
+    sld_status st = ensure_workspace(s, o.precision == SLD_FP32_IR, false);
+    if (st != SLD_OK) return st;
+    cudaError_t e = cudaMemcpyAsync(s->bwork, s->b, sizeof(double) * s->g.n, cudaMemcpyDeviceToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "batch rhs");
+  }
+  sld_batch bt = new sld_batch_s();
+  bt->sys.assign(systems, systems + count);
+  bt->o = o;
+  cudaEventCreate(&bt->ev0);
+  cudaEventCreate(&bt->ev1);
+  {
+    cudaError_t e = cudaStreamCreateWithFlags(&bt->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      sld_batch_destroy(bt);
+      return cuda_fail(e, "batch stream");
+    }
+  }
+  // candidate launch shapes: CTAs per SM, team-size exponent, cells per lane
+  bool all4 = true;
+  for (int k = 0; k < count; ++k) all4 = all4 && systems[k]->g.nx % 4 == 0 && systems[k]->g.nx >= 96;
+  struct Cand { int per; double expo; int cx; };
+  std::vector<Cand> cands;
+  for (int cx : (all4 ? std::vector<int>{1, 4} : std::vector<int>{1}))
+    for (double ex : {1.0, 4.0 / 3.0}) cands.push_back({o.ctas_per_sm, ex, cx});
+  if (o.ctas_per_sm > 0) cands = {{o.ctas_per_sm, 4.0 / 3.0, all4 ? 4 : 1}};
+  std::string times;
+  float best_ms = 0.f;
+  for (size_t c = 0; c < cands.size(); ++c) {
+    sld::BatchPlan trial;
+    std::string msg;
+    int st = sld::batch_build(bt->sys.data(), count, o, cands[c].per, cands[c].expo, cands[c].cx, bt->stream, &trial,
+                              &msg);
+    if (st != SLD_OK) {
+      sld::batch_free(&trial);
+      if (cands.size() == 1 || c + 1 == cands.size()) {
+        if (!bt->plan.exec) {
+          sld_batch_destroy(bt);
+          return fail((sld_status)st, msg);
+        }
+      }
+      continue;
+    }
+    float ms = 0.f;
+    if (cands.size() > 1) {  // time one full batched solve with this shape
+      std::swap(bt->plan, trial);
+      sld_status ls = batch_launch(bt, &ms);
+      std::swap(bt->plan, trial);
+      if (ls != SLD_OK) {
+        sld::batch_free(&trial);
+        sld_batch_destroy(bt);
+        return ls;
+      }
+      times += " [cx " + std::to_string(cands[c].cx) + ", expo " + std::to_string(cands[c].expo).substr(0, 4) +
+               ": " + std::to_string(ms).substr(0, 7) + " ms]";
+    }
+    if (!bt->plan.exec || ms < best_ms) {
+      sld::batch_free(&bt->plan);
+      bt->plan = trial;
+      best_ms = ms;
+    } else {
+      sld::batch_free(&trial);
+    }
+  }
+  const sld::BatchPlan& p = bt->plan;
+  bt->desc = "systems " + std::to_string(count) + ", CTAs " + std::to_string(p.G) + " (" + std::to_string(p.per_sm) +
+             " per SM), cells per lane " + std::to_string(p.cx) + ", team exponent " +
+             std::to_string(p.expo).substr(0, 4) + ", teams";
+  for (int k = 0; k < count; ++k) bt->desc += " " + std::to_string(p.teams[k]);
+  if (!times.empty()) bt->desc += "; autotune:" + times;
+  *out = bt;
+  return SLD_OK;
+}
+
+sld_status sld_batch_solve(sld_batch bt, const double* const* b, double* const* x, sld_result* res) {
+  g_last_error.clear();
+  if (!bt) return fail(SLD_ERR_INVALID_ARG, "batch is NULL");
+  const int count = (int)bt->sys.size();
+  for (int k = 0; k < count; ++k) {
+    sld_system s = bt->sys[k];
+    const double* src = (b && b[k]) ? b[k] : s->b;
+    cudaError_t e = cudaMemcpyAsync(s->bwork, src, sizeof(double) * s->g.n, kind_in(src), s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "batch rhs");
+  }
+  float ms = 0.f;
+  sld_status st = batch_launch(bt, &ms);
+  if (st != SLD_OK) return st;
+  sld_status worst = SLD_OK;
+  std::string first_msg;
+  for (int k = 0; k < count; ++k) {
+    sld_result r{};
+    sld_status sk = collect(bt->sys[k], bt->sys[k]->bwork, ms, x ? x[k] : nullptr, &r);
+    if (res) res[k] = r;
+    if (sk != SLD_OK && worst == SLD_OK) {
+      worst = sk;
+      first_msg = "system " + std::to_string(k) + ": " + g_last_error;
+    }
+  }
+  if (worst != SLD_OK) return fail(worst, first_msg);
+  return SLD_OK;
+}
+
+const char* sld_batch_describe(sld_batch bt) { return bt ? bt->desc.c_str() : ""; }
+
+void sld_batch_destroy(sld_batch bt) {
+  if (!bt) return;
+  if (bt->stream) cudaStreamSynchronize(bt->stream);
+  sld::batch_free(&bt->plan);
+  if (bt->stream) cudaStreamDestroy(bt->stream);
+  if (bt->ev0) cudaEventDestroy(bt->ev0);
+  if (bt->ev1) cudaEventDestroy(bt->ev1);
+  delete bt;
+}
+
+sld_status sld_solve_batched(sld_system* systems, int count, const double* const* b, const sld_options* o,
+                             double* const* x, sld_result* res) {
+  sld_batch bt = nullptr;
+  sld_status st = sld_batch_create(systems, count, o, &bt);
+  if (st != SLD_OK) return st;
+  st = sld_batch_solve(bt, b, x, res);
+  sld_batch_destroy(bt);
+  return st;
 }
 
 }  // extern "C"

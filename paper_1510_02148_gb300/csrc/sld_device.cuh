@@ -27,9 +27,9 @@ __device__ __forceinline__ int ld_volatile_i32(const int* p) {
   return *reinterpret_cast<const volatile int*>(p);
 }
 
-// Grid-wide barrier for a cooperative launch (all CTAs co-resident).
+// Barrier of a team of CTAs in a cooperative launch (all CTAs co-resident).
 // A monotone arrival counter: barrier number e completes when the counter
-// reaches e * gridDim.x.  Every wait is bounded by sy.timeout_ns; on expiry
+// reaches e * (team size).  Every wait is bounded by sy.timeout_ns; on expiry
 // the CTA records SLD_ERR_TIMEOUT in *sy.status and the barrier returns
 // false, as it does when another CTA has already recorded an error.  The
 // caller then leaves the kernel.  No trap, no unbounded spin.
@@ -38,8 +38,8 @@ __device__ __forceinline__ bool grid_barrier(const SyncArgs& sy, unsigned& epoch
   __syncthreads();
   if (threadIdx.x == 0) {
     ++epoch;
-    const unsigned target = epoch * gridDim.x;
-    const bool skip = sy.skip_epoch > 0 && blockIdx.x == 0 && epoch == (unsigned)sy.skip_epoch;
+    const unsigned target = epoch * (unsigned)sy.ncta;
+    const bool skip = sy.skip_epoch > 0 && (int)blockIdx.x == sy.cta0 && epoch == (unsigned)sy.skip_epoch;
     __threadfence();
     if (!skip) atomicAdd(sy.count, 1u);
     int ok = 1;
@@ -124,6 +124,9 @@ __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
   return v;
 }
+
+// Rank of this CTA in its team, and the team size.
+__device__ __forceinline__ int team_rank(const SyncArgs& sy) { return (int)blockIdx.x - sy.cta0; }
 
 // Dirichlet-cell test along one axis: coordinate c on a Dirichlet face.
 __device__ __forceinline__ bool dir_axis(int c, int n, unsigned lo, unsigned hi) {

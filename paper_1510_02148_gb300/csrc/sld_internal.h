@@ -22,7 +22,8 @@ constexpr int kWarpAccMaxD = 256;       // per-warp label accumulators up to thi
 constexpr int kPartScalars = 8;         // scalar slots after the d label sums
 
 struct SyncArgs {
-  unsigned* count;                // arrival counter, zeroed before the launch
+  unsigned* count;                // arrival counter of the team, zeroed before the launch
+  int cta0, ncta;                 // the team: CTAs cta0 .. cta0+ncta-1 of the launch
   int* status;                    // 0 or an sld_status, written on error
   unsigned long long timeout_ns;  // bound on every wait
   int skip_epoch;                 // test hook: CTA 0 does not arrive at this barrier (0 = off)
@@ -34,7 +35,9 @@ struct Geo {
   unsigned dlo_x, dhi_x, dlo_y, dhi_y, dlo_z, dhi_z;  // Dirichlet faces
 };
 
-// Everything the persistent solve kernel reads and writes.
+// Everything the persistent solve kernel reads and writes for one system.
+// The system is solved by a team of CTAs (all of them for a single solve,
+// a share of them in a batched solve): sy.cta0 .. sy.cta0 + sy.ncta - 1.
 struct SolveArgs {
   Geo g;
   int cx;                 // cells per lane in x (1 or 4)
@@ -128,6 +131,25 @@ int launch_solve_tma(sld_system s, SolveArgs& a, const sld_options& o, float* ms
 // sld_api.cu: the thread-local message returned by sld_last_error()
 void set_last_error(const std::string& msg);
 // sld_solve.cu
+void fill_args(sld_system s, const double* b_dev, const sld_options& o, SolveArgs* a);
 int run_solve(sld_system s, const double* b_dev, const sld_options& o, sld_result* res,
               std::string* msg);  // returns sld_status
+
+// A batched solve: one cooperative launch over all systems, each solved by
+// its own team of CTAs, captured with its state resets in a CUDA graph.
+struct BatchPlan {
+  int count = 0, G = 0, cx = 1, per_sm = 0;
+  double expo = 1.0;
+  bool fp64 = false, wacc = true;
+  size_t smem = 0;
+  SolveArgs* d_args = nullptr;
+  int* d_cta = nullptr;
+  cudaStream_t stream = nullptr;  // the batch's own stream (capture and launch), not owned here
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int teams[4096];
+};
+int batch_build(sld_system* sys, int count, const sld_options& o, int per_sm, double expo, int cx,
+                cudaStream_t stream, BatchPlan* plan, std::string* msg);
+void batch_free(BatchPlan* plan);
 }  // namespace sld

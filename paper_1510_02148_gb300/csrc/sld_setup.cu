@@ -451,13 +451,19 @@ int coarse_factor(sld_system s, const double* E, double* Einv, double timeout_s,
   cudaMemcpyAsync(A, E, mat, cudaMemcpyDeviceToDevice, s->stream);
   cudaMemsetAsync(Lm, 0, mat, s->stream);
   cudaMemsetAsync(bar, 0, 64, s->stream);
-  SyncArgs sy{bar, st, (unsigned long long)(timeout_s * 1e9), 0};
+  SyncArgs sy{};
+  sy.count = bar;
+  sy.status = st;
+  sy.timeout_ns = (unsigned long long)(timeout_s * 1e9);
+  sy.skip_epoch = 0;
   const size_t smem = sizeof(double) * d;
   cudaFuncSetAttribute(k_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int per = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cholesky, 256, smem);
   int G = std::max(1, std::min(s->nsm * std::max(per, 1), (d + 7) / 8));
   if (per < 1) G = 1;
+  sy.cta0 = 0;
+  sy.ncta = G;
   void* args[] = {(void*)&d, (void*)&A, (void*)&Lm, (void*)&sy};
   e = cudaLaunchCooperativeKernel((void*)k_cholesky, dim3(G), dim3(256), args, smem, s->stream);
   int hst = 0;

@@ -27,6 +27,7 @@
 // it is x = x + xhat + Z E^{-1} Z^T (b - A (x + xhat)), i.e. x* + P^T xhat.
 #include <cstdlib>
 #include <cstring>
+#include <vector>
 
 #include "sld_solve_common.cuh"
 
@@ -166,7 +167,8 @@ __device__ void sweep_A(const SolveArgs& a, const Sm<T>& sm, const T* zb, const 
   LabelAcc<T, WACC> la;
   la.init(a.lab_L);
   double dgam = 0.0;
-  const int64_t t0 = a.ntiles * blockIdx.x / gridDim.x, t1 = a.ntiles * (blockIdx.x + 1) / gridDim.x;
+  const int tr = team_rank(a.sy);
+  const int64_t t0 = a.ntiles * tr / a.sy.ncta, t1 = a.ntiles * (tr + 1) / a.sy.ncta;
   for (int64_t t = t0; t < t1;) {
     const int64_t ct = t / g.nz;
     const int z0 = (int)(t % g.nz);
@@ -324,7 +326,8 @@ __device__ void sweep_B(const SolveArgs& a, const Sm<T>& sm, const T* p, T* zb, 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const T* Y = sm.Y;
   double drho = 0.0, drr = 0.0;
-  const int64_t t0 = a.ntiles * blockIdx.x / gridDim.x, t1 = a.ntiles * (blockIdx.x + 1) / gridDim.x;
+  const int tr = team_rank(a.sy);
+  const int64_t t0 = a.ntiles * tr / a.sy.ncta, t1 = a.ntiles * (tr + 1) / a.sy.ncta;
   for (int64_t t = t0; t < t1;) {
     const int64_t ct = t / g.nz;
     const int z0 = (int)(t % g.nz);
@@ -482,8 +485,7 @@ __device__ void sweep_B(const SolveArgs& a, const Sm<T>& sm, const T* p, T* zb, 
 }
 
 template <typename T, int CX, bool WACC>
-__global__ void __launch_bounds__(kThreads) k_solve(SolveArgs a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void solve_generic(const SolveArgs& a, unsigned char* smem_raw) {
   const Sm<T> sm = carve<T, CX, WACC>(smem_raw, a.d);
   const T* Fx = static_cast<const T*>(a.Txi);
   const T* Fy = static_cast<const T*>(a.Tyi);
@@ -501,6 +503,26 @@ __global__ void __launch_bounds__(kThreads) k_solve(SolveArgs a) {
         sweep_B<T, CX, WACC>(a, sm, pb[pn], zb, xh, alpha, Fx, Fy, Fz, part);
         return true;
       });
+}
+
+template <typename T, int CX, bool WACC>
+__global__ void __launch_bounds__(kThreads) k_solve(SolveArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  solve_generic<T, CX, WACC>(a, smem_raw);
+}
+
+// Batched solve: CTA c works on system cta_sys[c] with the team of CTAs the
+// host assigned to it (its barriers, reductions and partial sums are the
+// team's own); teams never wait on each other, and a team leaves the kernel
+// as soon as its system is solved.
+template <typename T, int CX, bool WACC>
+__global__ void __launch_bounds__(kThreads) k_solve_batch(const SolveArgs* __restrict__ all,
+                                                         const int* __restrict__ cta_sys) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ SolveArgs a;
+  if (threadIdx.x == 0) a = all[cta_sys[blockIdx.x]];
+  __syncthreads();
+  solve_generic<T, CX, WACC>(a, smem_raw);
 }
 
 template <typename T, int CX, bool WACC>
@@ -522,6 +544,8 @@ int launch(sld_system s, SolveArgs& a, const sld_options& o, float* ms, std::str
   int G = s->nsm * per;
   G = (int)std::max<int64_t>(1, std::min<int64_t>(G, a.ntiles));
   if (G > s->part_rows) G = s->part_rows;
+  a.sy.cta0 = 0;
+  a.sy.ncta = G;
   void* args[] = {&a};
   cudaEventRecord(s->ev0, s->stream);
   e = cudaLaunchCooperativeKernel((void*)kern, dim3(G), dim3(kThreads), args, smem, s->stream);
@@ -542,10 +566,10 @@ int launch(sld_system s, SolveArgs& a, const sld_options& o, float* ms, std::str
 
 }  // namespace
 
-int run_solve(sld_system s, const double* b_dev, const sld_options& o, sld_result* res, std::string* msg) {
-  const int64_t n = s->g.n;
+void fill_args(sld_system s, const double* b_dev, const sld_options& o, SolveArgs* ap) {
+  SolveArgs& a = *ap;
+  a = SolveArgs{};
   const bool fp64 = o.precision == SLD_FP64;
-  SolveArgs a{};
   a.g = s->g;
   a.cx = (s->g.nx % 4 == 0 && s->g.nx >= 96) ? 4 : 1;
   const int TX = 32 * a.cx;
@@ -603,6 +627,14 @@ int run_solve(sld_system s, const double* b_dev, const sld_options& o, sld_resul
   a.maxiter = o.maxiter;
   a.max_outer = fp64 ? 1 : o.max_outer;
   a.fp64 = fp64 ? 1 : 0;
+}
+
+int run_solve(sld_system s, const double* b_dev, const sld_options& o, sld_result* res, std::string* msg) {
+  const int64_t n = s->g.n;
+  const bool fp64 = o.precision == SLD_FP64;
+  const bool bf16 = o.precision == SLD_BF16COEF_IR;
+  SolveArgs a;
+  fill_args(s, b_dev, o, &a);
   // x = 0; the inner state is set by the first refinement step
   cudaMemsetAsync(s->x, 0, sizeof(double) * n, s->stream);
   cudaMemsetAsync(s->xh, 0, sizeof(double) * n, s->stream);
@@ -649,6 +681,183 @@ int run_solve(sld_system s, const double* b_dev, const sld_options& o, sld_resul
   if (code == SLD_ERR_NOT_CONVERGED) *msg = "not converged within maxiter / max_outer";
   if (code == SLD_ERR_BREAKDOWN) *msg = "breakdown: p^T P A p <= 0 or a non-finite scalar";
   return code;
+}
+
+
+// ---------------------------------------------------------------------------
+// Batched solve plan.
+// ---------------------------------------------------------------------------
+namespace {
+
+template <typename T, int CX, bool WACC>
+int batch_capture(sld_system s0, BatchPlan* p, sld_system* sys, std::string* msg) {
+  auto kern = k_solve_batch<T, CX, WACC>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem);
+  if (e != cudaSuccess) {
+    *msg = std::string("batch kernel attribute: ") + cudaGetErrorString(e);
+    return SLD_ERR_CUDA;
+  }
+  (void)s0;
+  cudaStream_t st = p->stream;
+  e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    *msg = std::string("graph capture: ") + cudaGetErrorString(e);
+    return SLD_ERR_CUDA;
+  }
+  for (int k = 0; k < p->count; ++k) {
+    sld_system s = sys[k];
+    cudaMemsetAsync(s->x, 0, sizeof(double) * s->g.n, st);
+    cudaMemsetAsync(s->xh, 0, sizeof(double) * s->g.n, st);
+    cudaMemsetAsync(s->bar, 0, 64, st);
+    cudaMemsetAsync(s->out, 0, sizeof(double) * kOutCount, st);
+    cudaMemsetAsync(s->status, 0, sizeof(int) * 4, st);
+  }
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(p->G);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = p->smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const SolveArgs* da = p->d_args;
+  const int* dc = p->d_cta;
+  cudaError_t el = cudaLaunchKernelEx(&cfg, kern, da, dc);
+  e = cudaStreamEndCapture(st, &p->graph);
+  if (el != cudaSuccess || e != cudaSuccess) {
+    *msg = std::string("batch capture: ") + cudaGetErrorString(el != cudaSuccess ? el : e);
+    return SLD_ERR_CUDA;
+  }
+  e = cudaGraphInstantiate(&p->exec, p->graph, 0);
+  if (e != cudaSuccess) {
+    *msg = std::string("graph instantiate: ") + cudaGetErrorString(e);
+    return SLD_ERR_CUDA;
+  }
+  return SLD_OK;
+}
+
+template <typename T, int CX, bool WACC>
+int batch_occupancy(size_t smem) {
+  auto kern = k_solve_batch<T, CX, WACC>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int per = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kThreads, smem);
+  return per;
+}
+
+template <typename T, int CX, bool WACC>
+size_t batch_smem(int dmax) {
+  return smem_bytes<T, CX, WACC>(dmax);
+}
+
+}  // namespace
+
+void batch_free(BatchPlan* p) {
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  if (p->d_args) cudaFree(p->d_args);
+  if (p->d_cta) cudaFree(p->d_cta);
+  p->exec = nullptr;
+  p->graph = nullptr;
+  p->d_args = nullptr;
+  p->d_cta = nullptr;
+}
+
+// Teams: system k gets a share of the CTAs proportional to n_k^expo (work per
+// iteration grows with n, the iteration count roughly with the side), at
+// least one CTA, at most one per plane tile and per partial-sum row.
+int batch_build(sld_system* sys, int count, const sld_options& o, int per_sm, double expo, int cx,
+                cudaStream_t stream, BatchPlan* p, std::string* msg) {
+  sld_system s0 = sys[0];
+  p->stream = stream;
+  p->count = count;
+  p->fp64 = o.precision == SLD_FP64;
+  p->cx = cx;
+  p->expo = expo;
+  int dmax = 1;
+  for (int k = 0; k < count; ++k) dmax = std::max(dmax, sys[k]->d);
+  p->wacc = dmax <= kWarpAccMaxD;
+#define SLD_BATCH_DISPATCH(FN, ...)                                                              \
+  (p->fp64 ? (cx == 4 ? (p->wacc ? FN<double, 4, true>(__VA_ARGS__) : FN<double, 4, false>(__VA_ARGS__)) \
+                      : (p->wacc ? FN<double, 1, true>(__VA_ARGS__) : FN<double, 1, false>(__VA_ARGS__))) \
+           : (cx == 4 ? (p->wacc ? FN<float, 4, true>(__VA_ARGS__) : FN<float, 4, false>(__VA_ARGS__))   \
+                      : (p->wacc ? FN<float, 1, true>(__VA_ARGS__) : FN<float, 1, false>(__VA_ARGS__))))
+  p->smem = SLD_BATCH_DISPATCH(batch_smem, dmax);
+  int occ = SLD_BATCH_DISPATCH(batch_occupancy, p->smem);
+  if (occ < 1) {
+    *msg = "batch kernel does not fit on an SM";
+    return SLD_ERR_CUDA;
+  }
+  p->per_sm = per_sm > 0 ? std::min(per_sm, occ) : occ;
+  int G = s0->nsm * p->per_sm;
+  if (count > G) {
+    *msg = "more systems (" + std::to_string(count) + ") than co-resident CTAs (" + std::to_string(G) + ")";
+    return SLD_ERR_INVALID_ARG;
+  }
+  std::vector<SolveArgs> args(count);
+  std::vector<double> w(count), ideal(count);
+  std::vector<int> cap(count);
+  double wsum = 0.0;
+  for (int k = 0; k < count; ++k) {
+    fill_args(sys[k], sys[k]->bwork, o, &args[k]);
+    SolveArgs& a = args[k];
+    a.cx = cx;
+    const int TX = 32 * cx;
+    a.ntx = (a.g.nx + TX - 1) / TX;
+    a.nty = (a.g.ny + kTY - 1) / kTY;
+    a.ntiles = (int64_t)a.ntx * a.nty * a.g.nz;
+    cap[k] = (int)std::min<int64_t>(std::min<int64_t>(a.ntiles, sys[k]->part_rows), G);
+    w[k] = std::pow((double)a.g.n, expo);
+    wsum += w[k];
+  }
+  int used = 0;
+  for (int k = 0; k < count; ++k) {
+    ideal[k] = G * w[k] / wsum;
+    p->teams[k] = std::max(1, std::min(cap[k], (int)ideal[k]));
+    used += p->teams[k];
+  }
+  while (used > G) {  // give back from the largest teams
+    int j = 0;
+    for (int k = 1; k < count; ++k)
+      if (p->teams[k] > p->teams[j]) j = k;
+    if (p->teams[j] <= 1) break;
+    --p->teams[j];
+    --used;
+  }
+  while (used < G) {  // hand out the rest where the share is most short
+    int j = -1;
+    double best = -1e300;
+    for (int k = 0; k < count; ++k)
+      if (p->teams[k] < cap[k] && ideal[k] - p->teams[k] > best) {
+        best = ideal[k] - p->teams[k];
+        j = k;
+      }
+    if (j < 0) break;
+    ++p->teams[j];
+    ++used;
+  }
+  p->G = used;
+  std::vector<int> cta_sys;
+  cta_sys.reserve(used);
+  for (int k = 0; k < count; ++k) {
+    args[k].sy.cta0 = (int)cta_sys.size();
+    args[k].sy.ncta = p->teams[k];
+    for (int c = 0; c < p->teams[k]; ++c) cta_sys.push_back(k);
+  }
+  cudaError_t e = cudaMalloc(&p->d_args, sizeof(SolveArgs) * count);
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_cta, sizeof(int) * used);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(p->d_args, args.data(), sizeof(SolveArgs) * count, cudaMemcpyHostToDevice, stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(p->d_cta, cta_sys.data(), sizeof(int) * used, cudaMemcpyHostToDevice, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) {
+    *msg = std::string("batch plan: ") + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? SLD_ERR_OOM : SLD_ERR_CUDA;
+  }
+  return SLD_BATCH_DISPATCH(batch_capture, s0, p, sys, msg);
+#undef SLD_BATCH_DISPATCH
 }
 
 }  // namespace sld

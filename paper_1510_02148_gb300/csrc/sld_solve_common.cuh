@@ -209,10 +209,10 @@ __device__ void sweep_O1(const SolveArgs& a, double* sacc, double* red, double* 
   for (int k = threadIdx.x; k < (WACC ? kWarps : 1) * d; k += blockDim.x) sacc[k] = 0.0;
   __syncthreads();
   double bb = 0.0;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t stride = (int64_t)a.sy.ncta * blockDim.x;
   const int64_t nround = (g.n + stride - 1) / stride;
   for (int64_t rnd = 0; rnd < nround; ++rnd) {
-    const int64_t i = rnd * stride + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i = rnd * stride + (int64_t)team_rank(a.sy) * blockDim.x + threadIdx.x;
     const bool ok = i < g.n;
     double r = 0.0;
     int l = -1;
@@ -249,8 +249,8 @@ __device__ void sweep_O2(const SolveArgs& a, const double* Yd, double* red, doub
   T* p0 = static_cast<T*>(a.p0);
   T* p1 = static_cast<T*>(a.p1);
   double rr = 0.0, rho = 0.0;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < g.n; i += stride) {
+  const int64_t stride = (int64_t)a.sy.ncta * blockDim.x;
+  for (int64_t i = (int64_t)team_rank(a.sy) * blockDim.x + threadIdx.x; i < g.n; i += stride) {
     const int ix = (int)(i % g.nx), iy = (int)((i / g.nx) % g.ny), iz = (int)(i / g.nxy);
     const double AZy = apply64(a, i, ix, iy, iz, [&](int64_t j) { return Yd[__ldg(a.label + j)]; });
     const double rh = a.r64[i] - AZy;
@@ -279,8 +279,8 @@ __device__ void sweep_O2(const SolveArgs& a, const double* Yd, double* red, doub
 __device__ void phase_reduce_s(const SolveArgs& a) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nw = blockDim.x >> 5;
-  const int G = gridDim.x;
-  for (int k = blockIdx.x * nw + warp; k < a.d; k += G * nw) {
+  const int G = a.sy.ncta;
+  for (int k = team_rank(a.sy) * nw + warp; k < a.d; k += G * nw) {
     double t = 0.0;
     for (int c = lane; c < G; c += 32) t += a.part[(int64_t)c * a.pstride + k];
     t = warp_sum(t);
@@ -292,7 +292,7 @@ __device__ void phase_reduce_s(const SolveArgs& a) {
 __device__ void phase_coarse(const SolveArgs& a, const double* Einv) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nw = blockDim.x >> 5;
-  for (int j = blockIdx.x * nw + warp; j < a.d; j += gridDim.x * nw) {
+  for (int j = team_rank(a.sy) * nw + warp; j < a.d; j += a.sy.ncta * nw) {
     const double* row = Einv + (int64_t)j * a.d;
     double t = 0.0;
     for (int k = lane; k < a.d; k += 32) t += __ldg(row + k) * a.s_glob[k];
@@ -306,7 +306,7 @@ __device__ double cta_scalar(const SolveArgs& a, int slot, double* red) {
   __syncthreads();
   if (threadIdx.x < 32) {
     double t = 0.0;
-    for (int c = threadIdx.x; c < (int)gridDim.x; c += 32) t += a.part[(int64_t)c * a.pstride + a.d + slot];
+    for (int c = threadIdx.x; c < a.sy.ncta; c += 32) t += a.part[(int64_t)c * a.pstride + a.d + slot];
     t = warp_sum(t);
     if (threadIdx.x == 0) red[40] = t;
   }
@@ -340,7 +340,7 @@ __device__ double cta_sdoty(const SolveArgs& a, double* red) {
 template <typename T, bool WACC, class SweepA, class SweepB>
 __device__ void solve_body(const SolveArgs& a, double* acc, double* Yd, T* Y, double* red, SweepA&& sweepA,
                            SweepB&& sweepB) {
-  double* my_part = a.part + (int64_t)blockIdx.x * a.pstride;
+  double* my_part = a.part + (int64_t)team_rank(a.sy) * a.pstride;
   unsigned epoch = 0;
   const double tol2 = a.tol * a.tol;
   double bb = 0.0, rr_outer = 0.0, rho = 0.0, rec_rr = 0.0;
@@ -409,7 +409,7 @@ __device__ void solve_body(const SolveArgs& a, double* acc, double* Yd, T* Y, do
     }
     if (failed || status) break;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (team_rank(a.sy) == 0 && threadIdx.x == 0) {
     a.out[kOutIters] = its;
     a.out[kOutOuter] = outer;
     a.out[kOutRR] = rr_outer;

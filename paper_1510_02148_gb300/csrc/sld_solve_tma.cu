@@ -220,7 +220,8 @@ __device__ bool sweep_tma(const SolveArgs& a, const Maps& mp, const Ring<S>& rg,
   if constexpr (IS_A) {
     for (int k = tid; k < (WACC ? kWarps : 1) * d; k += blockDim.x) sacc[k] = 0.0;
   }
-  const int64_t t0 = a.ntiles * blockIdx.x / gridDim.x, t1 = a.ntiles * (blockIdx.x + 1) / gridDim.x;
+  const int tr = team_rank(a.sy);
+  const int64_t t0 = a.ntiles * tr / a.sy.ncta, t1 = a.ntiles * (tr + 1) / a.sy.ncta;
   const uint64_t first = gitem;
   uint64_t released = gitem;  // items below this are free
   uint64_t issued = gitem;    // thread 0 only
@@ -627,6 +628,8 @@ int launch_tma(sld_system s, SolveArgs& a, const sld_options& o, float* ms, std:
   int G = s->nsm * per;
   G = (int)std::max<int64_t>(1, std::min<int64_t>(G, a.ntiles));
   if (G > s->part_rows) G = s->part_rows;
+  a.sy.cta0 = 0;
+  a.sy.ncta = G;
   void* args[] = {&a, &mp, &ntx};
   cudaEventRecord(s->ev0, s->stream);
   e = cudaLaunchCooperativeKernel((void*)kern, dim3(G), dim3(16 * TY), args, smem, s->stream);

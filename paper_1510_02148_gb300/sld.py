@@ -28,7 +28,8 @@ BC_NOFLOW, BC_DIRICHLET = 0, 1
 
 EXPORTED = ["sld_default_options", "sld_build_system", "sld_make_labels", "sld_build_deflation",
             "sld_solve", "sld_destroy", "sld_last_error", "sld_get_operator", "sld_apply_A",
-            "sld_restrict", "sld_get_coarse"]
+            "sld_restrict", "sld_get_coarse", "sld_batch_create", "sld_batch_solve",
+            "sld_batch_describe", "sld_batch_destroy", "sld_solve_batched"]
 
 
 class SldError(RuntimeError):
@@ -83,8 +84,16 @@ def load(path: str = LIB_PATH):
         lib.sld_apply_A.argtypes = [P, P, P]
         lib.sld_restrict.argtypes = [P, P, P]
         lib.sld_get_coarse.argtypes = [P, P, P]
+        lib.sld_batch_create.argtypes = [P, C.c_int, C.POINTER(Options), C.POINTER(P)]
+        lib.sld_batch_solve.argtypes = [P, P, P, P]
+        lib.sld_batch_describe.argtypes = [P]
+        lib.sld_batch_describe.restype = C.c_char_p
+        lib.sld_batch_destroy.argtypes = [P]
+        lib.sld_batch_destroy.restype = None
+        lib.sld_solve_batched.argtypes = [P, C.c_int, P, C.POINTER(Options), P, P]
         for name in ("sld_build_system", "sld_make_labels", "sld_build_deflation", "sld_solve",
-                     "sld_get_operator", "sld_apply_A", "sld_restrict", "sld_get_coarse"):
+                     "sld_get_operator", "sld_apply_A", "sld_restrict", "sld_get_coarse",
+                     "sld_batch_create", "sld_batch_solve", "sld_solve_batched"):
             getattr(lib, name).restype = C.c_int
         _lib = lib
         return lib
@@ -234,3 +243,51 @@ def from_problem(P, stream=None) -> System:
     s.make_labels(P.S, P.tau, P.L)
     s.build_deflation(P.d)
     return s
+
+
+class Batch:
+    """A batched-solve plan over several Systems (sld_batch): one persistent
+    launch, one team of CTAs per system, captured in a CUDA graph."""
+
+    def __init__(self, systems: Sequence[System], options: Optional[Options] = None, **kw):
+        lib = load()
+        self.systems = list(systems)
+        o = options if options is not None else default_options(**kw)
+        arr = (C.c_void_p * len(self.systems))(*[s._h.value for s in self.systems])
+        h = C.c_void_p()
+        _check(lib.sld_batch_create(arr, len(self.systems), C.byref(o), C.byref(h)))
+        self._h = h
+        self._arr = arr
+
+    def describe(self) -> str:
+        return load().sld_batch_describe(self._h).decode()
+
+    def solve(self, bs=None, xs=None, raise_on_error=True):
+        """bs, xs: sequences (one entry per system, None = assembled rhs /
+        allocate a host array).  Returns (xs, infos)."""
+        n = len(self.systems)
+        if xs is None:
+            xs = [np.empty(s.n, dtype=np.float64) for s in self.systems]
+        bptr = None
+        if bs is not None:
+            bptr = (C.c_void_p * n)(*[None if b is None else _ptr(b, np.float64) for b in bs])
+        xptr = (C.c_void_p * n)(*[_ptr(x, np.float64) for x in xs])
+        res = (Result * n)()
+        st = load().sld_batch_solve(self._h, bptr, xptr, res)
+        infos = [SolveInfo(r.iterations, r.outer_steps, r.true_relres, r.recursive_relres, r.solve_ms, st,
+                           r.kernel_path) for r in res]
+        if st != OK and raise_on_error:
+            _check(st)
+        return xs, infos
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().sld_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
