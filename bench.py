@@ -132,6 +132,46 @@ def cpu_baseline(P, A=None, lab=None, iters_full=None, sample_iters=40, threads=
                       f"scaled to {full} iterations"}
 
 
+def bench_batched(sld, torch, reps=3):
+    """64 independent layered cubes (side ~ U{32..160}) in one batched
+    persistent launch (FP32 inner, FP64 refinement), against the same
+    systems solved one at a time."""
+    from paper_1510_02148_gb300 import workloads as W
+    probs = W.batch(64, seed=1)
+    systems = []
+    for P in probs:
+        s = sld.System(torch.from_numpy(P.K.reshape(-1)).cuda(), None, P.bc_type, P.bc_value, shape=P.shape)
+        s.make_labels(P.S, P.tau, P.L)
+        s.build_deflation(P.d)
+        systems.append(s)
+    xs = [torch.empty(P.n, dtype=torch.float64, device="cuda") for P in probs]
+    t0 = time.perf_counter()
+    bt = sld.Batch(systems, precision=sld.FP32_IR)
+    plan_s = time.perf_counter() - t0
+    bt.solve(xs=xs)
+    times = []
+    infos = None
+    for _ in range(reps):
+        _, infos = bt.solve(xs=xs)
+        times.append(infos[0].solve_ms)
+    ms = statistics.median(times)
+    seq = 0.0
+    for s, x in zip(systems, xs):
+        _, i1 = s.solve(x=x, precision=sld.FP32_IR)
+        seq += i1.solve_ms
+    cells = sum(P.n for P in probs)
+    alg = sum(P.n * (64 * i.iterations + BYTES_OUTER * i.outer_steps) for P, i in zip(probs, infos))
+    out = {"systems": len(probs), "cells": cells, "ms": ms, "solves_per_s": len(probs) / (ms * 1e-3),
+           "alg_gbs": alg / (ms * 1e-3) / 1e9, "iterations_total": sum(i.iterations for i in infos),
+           "max_true_relres": max(i.true_relres for i in infos),
+           "one_at_a_time_ms": seq, "speedup_vs_one_at_a_time": seq / ms, "plan": bt.describe(),
+           "plan_and_tune_s": plan_s}
+    bt.close()
+    for s in systems:
+        s.close()
+    return out
+
+
 def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
@@ -167,6 +207,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=2)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -273,6 +314,8 @@ def main():
         "gpu_launches": 3 * args.steps,
         "clocks": clk.summary(),
     }
+    if not args.no_batched:
+        line["batched"] = bench_batched(sld, torch)
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(P, iters_full=fp64[-1].iterations, sample_iters=30)
     s.close()

@@ -549,8 +549,8 @@ sld_status sld_batch_create(sld_system* systems, int count, const sld_options* o
   for (size_t c = 0; c < cands.size(); ++c) {
     sld::BatchPlan trial;
     std::string msg;
-    int st = sld::batch_build(bt->sys.data(), count, o, cands[c].per, cands[c].expo, cands[c].cx, bt->stream, &trial,
-                              &msg);
+    int st = sld::batch_build(bt->sys.data(), count, o, cands[c].per, cands[c].expo, nullptr, cands[c].cx, bt->stream,
+                              &trial, &msg);
     if (st != SLD_OK) {
       sld::batch_free(&trial);
       if (cands.size() == 1 || c + 1 == cands.size()) {
@@ -582,10 +582,48 @@ sld_status sld_batch_create(sld_system* systems, int count, const sld_options* o
       sld::batch_free(&trial);
     }
   }
+  // one more candidate: teams proportional to each system's measured work
+  // (cells x iterations of the trial solves), the same launch shape
+  if (cands.size() > 1 && bt->plan.exec) {
+    std::vector<double> wk(count);
+    bool okw = true;
+    for (int k = 0; k < count && okw; ++k) {
+      double out[sld::kOutCount];
+      sld_system s = systems[k];
+      okw = cudaMemcpy(out, s->out, sizeof(out), cudaMemcpyDeviceToHost) == cudaSuccess;
+      const double its = out[sld::kOutIters] + 3.0 * out[sld::kOutOuter];
+      wk[k] = (double)s->g.n * std::max(its, 1.0);
+    }
+    sld::BatchPlan trial;
+    std::string msg;
+    if (okw && sld::batch_build(bt->sys.data(), count, o, bt->plan.per_sm, 1.0, wk.data(), bt->plan.cx, bt->stream,
+                                &trial, &msg) == SLD_OK) {
+      float ms = 0.f;
+      std::swap(bt->plan, trial);
+      sld_status ls = batch_launch(bt, &ms);
+      std::swap(bt->plan, trial);
+      if (ls != SLD_OK) {
+        sld::batch_free(&trial);
+        sld_batch_destroy(bt);
+        return ls;
+      }
+      times += " [measured work: " + std::to_string(ms).substr(0, 7) + " ms]";
+      if (ms < best_ms) {
+        sld::batch_free(&bt->plan);
+        bt->plan = trial;
+        bt->plan.expo = -1.0;  // marks the measured-work plan
+        best_ms = ms;
+      } else {
+        sld::batch_free(&trial);
+      }
+    } else {
+      sld::batch_free(&trial);
+    }
+  }
   const sld::BatchPlan& p = bt->plan;
   bt->desc = "systems " + std::to_string(count) + ", CTAs " + std::to_string(p.G) + " (" + std::to_string(p.per_sm) +
-             " per SM), cells per lane " + std::to_string(p.cx) + ", team exponent " +
-             std::to_string(p.expo).substr(0, 4) + ", teams";
+             " per SM), cells per lane " + std::to_string(p.cx) + ", teams by " +
+             (p.expo < 0 ? std::string("measured work") : "n^" + std::to_string(p.expo).substr(0, 4)) + ":";
   for (int k = 0; k < count; ++k) bt->desc += " " + std::to_string(p.teams[k]);
   if (!times.empty()) bt->desc += "; autotune:" + times;
   *out = bt;

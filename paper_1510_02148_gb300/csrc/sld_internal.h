@@ -149,7 +149,8 @@ struct BatchPlan {
   cudaGraphExec_t exec = nullptr;
   int teams[4096];
 };
-int batch_build(sld_system* sys, int count, const sld_options& o, int per_sm, double expo, int cx,
-                cudaStream_t stream, BatchPlan* plan, std::string* msg);
+// weights: team shares (count values), or nullptr for n^expo
+int batch_build(sld_system* sys, int count, const sld_options& o, int per_sm, double expo, const double* weights,
+                int cx, cudaStream_t stream, BatchPlan* plan, std::string* msg);
 void batch_free(BatchPlan* plan);
 }  // namespace sld

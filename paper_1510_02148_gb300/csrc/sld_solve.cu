@@ -152,7 +152,18 @@ __device__ __forceinline__ Seg make_seg(const SolveArgs& a, int64_t ct, int z0, 
 
 // ---------------------------------------------------------------------------
 // Sweep A: p = z + beta p_old, v = A p, s = Z^T v, gamma = p . v
+//
+// Software pipeline: at step z a lane issues the loads of plane z+2's z and
+// p_old (its z+1 neighbour one step later), plane z+1's faces and labels,
+// and its x-halo values of plane z+1, and consumes them a step later; the
+// halo-row warps likewise load plane z+1 while publishing plane z.
 // ---------------------------------------------------------------------------
+template <typename T, int CX>
+struct FacesA {
+  T fx[CX], fy[CX], fz[CX], dg[CX];
+  int lb[CX];
+};
+
 template <typename T, int CX, bool WACC>
 __device__ void sweep_A(const SolveArgs& a, const Sm<T>& sm, const T* zb, const T* pold, T* pnew, T beta,
                         const T* __restrict__ Fx, const T* __restrict__ Fy, const T* __restrict__ Fz,
@@ -175,25 +186,66 @@ __device__ void sweep_A(const SolveArgs& a, const Sm<T>& sm, const T* zb, const 
     const int z1 = (int)((int64_t)g.nz < (int64_t)z0 + (t1 - t) ? (int64_t)g.nz : (int64_t)z0 + (t1 - t));
     t += z1 - z0;
     const Seg sg = make_seg<TX>(a, ct, z0, z1, CX);
-    // p_new at this lane's cells of plane zz (0 outside the grid)
-    auto pnew_at = [&](int zz, T(&o)[CX]) {
+    // raw z and p_old of this lane's cells of plane zz (0 outside the grid)
+    auto ld_raw = [&](int zz, T(&zv)[CX], T(&po)[CX]) {
+      if (zz < 0 || zz >= g.nz || sg.nv == 0) {
+#pragma unroll
+        for (int c = 0; c < CX; ++c) zv[c] = po[c] = T(0);
+        return;
+      }
+      const int64_t i = (int64_t)zz * g.nxy + sg.rowbase;
+      ld_cells<T, CX, false>(zb, i, sg.nv, zv);
+      ld_cells<T, CX, false>(pold, i, sg.nv, po);
+    };
+    auto ld_faces = [&](int zz, FacesA<T, CX>& f) {
+      if (zz < 0 || zz >= g.nz || sg.nv == 0) {
+#pragma unroll
+        for (int c = 0; c < CX; ++c) {
+          f.fx[c] = f.fy[c] = f.fz[c] = f.dg[c] = T(0);
+          f.lb[c] = -1;
+        }
+        return;
+      }
+      const int64_t i = (int64_t)zz * g.nxy + sg.rowbase;
+      ld_cells<T, CX, true>(Fx, i, sg.nv, f.fx);
+      ld_cells<T, CX, true>(Fy, i, sg.nv, f.fy);
+      ld_cells<T, CX, true>(Fz, i, sg.nv, f.fz);
+      ld_labels<CX>(a.label, i, sg.nv, f.lb);
+      if constexpr (sizeof(T) == 8) {
+        ld_cells<T, CX, true>(a.diag64, i, sg.nv, f.dg);
+      } else {
+#pragma unroll
+        for (int c = 0; c < CX; ++c) f.dg[c] = T(0);
+      }
+    };
+    auto ld_fy = [&](int zz, T(&o)[CX]) {
       if (zz < 0 || zz >= g.nz || sg.nv == 0) {
 #pragma unroll
         for (int c = 0; c < CX; ++c) o[c] = T(0);
         return;
       }
-      T zv[CX], po[CX];
-      const int64_t i = (int64_t)zz * g.nxy + sg.rowbase;
-      ld_cells<T, CX, false>(zb, i, sg.nv, zv);
-      ld_cells<T, CX, false>(pold, i, sg.nv, po);
-#pragma unroll
-      for (int c = 0; c < CX; ++c) o[c] = zv[c] + beta * po[c];
+      ld_cells<T, CX, true>(Fy, (int64_t)zz * g.nxy + sg.rowbase, sg.nv, o);
     };
-    auto pnew_scalar = [&](int x, int zz) -> T {
-      const int64_t i = (int64_t)zz * g.nxy + (int64_t)sg.y * g.nx + x;
-      return zb[i] + beta * pold[i];
+    // x-halo values of plane zz: lane 0 the cell left of the tile (z, p_old,
+    // and the face between), lane 31 the cell right of it
+    const bool hl_ok = sg.own && lane == 0 && sg.x0 - 1 >= 0 && sg.y < g.ny;
+    const bool hr_ok = sg.own && lane == 31 && sg.x0 + TX < g.nx && sg.y < g.ny;
+    auto ld_xh = [&](int zz, T& zx, T& px, T& fxl) {
+      zx = px = fxl = T(0);
+      if (zz < 0 || zz >= g.nz) return;
+      const int64_t row = (int64_t)zz * g.nxy + (int64_t)sg.y * g.nx;
+      if (hl_ok) {
+        zx = zb[row + sg.x0 - 1];
+        px = pold[row + sg.x0 - 1];
+        fxl = __ldg(Fx + row + sg.x0 - 1);
+      } else if (hr_ok) {
+        zx = zb[row + sg.x0 + TX];
+        px = pold[row + sg.x0 + TX];
+      }
     };
-    T pm[CX], pc[CX], pn[CX], tzm[CX];
+    T pm[CX], pc[CX], pn[CX], tzm[CX], zv2[CX], po2[CX];
+    FacesA<T, CX> F, F1;
+    T xz0 = T(0), xp0 = T(0), xf0 = T(0), xz1 = T(0), xp1 = T(0), xf1 = T(0);
     bool dxc[CX], dxm[CX], dxp[CX];
 #pragma unroll
     for (int c = 0; c < CX; ++c) {
@@ -206,13 +258,25 @@ __device__ void sweep_A(const SolveArgs& a, const Sm<T>& sm, const T* zb, const 
     const bool dym = dir_axis(sg.y - 1, g.ny, g.dlo_y, g.dhi_y);
     const bool dyp = dir_axis(sg.y + 1, g.ny, g.dlo_y, g.dhi_y);
     if (sg.own) {
-      pnew_at(z0 - 1, pm);
-      pnew_at(z0, pc);
-      if (z0 > 0 && sg.nv > 0) ld_cells<T, CX, true>(Fz, (int64_t)(z0 - 1) * g.nxy + sg.rowbase, sg.nv, tzm);
-      else {
+      T zv[CX], po[CX];
+      ld_raw(z0 - 1, zv, po);
 #pragma unroll
-        for (int c = 0; c < CX; ++c) tzm[c] = T(0);
-      }
+      for (int c = 0; c < CX; ++c) pm[c] = zv[c] + beta * po[c];
+      ld_raw(z0, zv, po);
+#pragma unroll
+      for (int c = 0; c < CX; ++c) pc[c] = zv[c] + beta * po[c];
+      ld_raw(z0 + 1, zv, po);
+#pragma unroll
+      for (int c = 0; c < CX; ++c) pn[c] = zv[c] + beta * po[c];
+      ld_faces(z0, F);
+      FacesA<T, CX> Fm;
+      ld_faces(z0 - 1, Fm);
+#pragma unroll
+      for (int c = 0; c < CX; ++c) tzm[c] = Fm.fz[c];
+      ld_xh(z0, xz0, xp0, xf0);
+    } else {
+      ld_raw(z0, zv2, po2);  // halo rows: plane z0 in (zv2, po2)
+      if (warp == kTY) ld_fy(z0, F.fy);
     }
     T gam = T(0);
     for (int z = z0; z < z1; ++z) {
@@ -221,48 +285,43 @@ __device__ void sweep_A(const SolveArgs& a, const Sm<T>& sm, const T* zb, const 
       T* sTy = sm.Ty + buf * (kTY + 1) * TX;
       T* sTxh = sm.Txh + buf * kTY;
       const int64_t iz = (int64_t)z * g.nxy + sg.rowbase;
-      T fx[CX], fy[CX], fz[CX], dg[CX] = {};
-      int lb[CX];
       if (sg.own) {
-        pnew_at(z + 1, pn);
-        ld_cells<T, CX, true>(Fx, iz, sg.nv, fx);
-        ld_cells<T, CX, true>(Fy, iz, sg.nv, fy);
-        ld_cells<T, CX, true>(Fz, iz, sg.nv, fz);
-        ld_labels<CX>(a.label, iz, sg.nv, lb);
-        if constexpr (sizeof(T) == 8) ld_cells<T, CX, true>(a.diag64, iz, sg.nv, dg);
+        // prefetch: plane z+2 vectors, plane z+1 faces and x-halo values
+        ld_raw(z + 2, zv2, po2);
+        ld_faces(z + 1, F1);
+        ld_xh(z + 1, xz1, xp1, xf1);
         sm_st<T, CX>(sP + (warp + 1) * RS + HOFF + lane * CX, pc);
-        sm_st<T, CX>(sTy + (warp + 1) * TX + lane * CX, fy);
+        sm_st<T, CX>(sTy + (warp + 1) * TX + lane * CX, F.fy);
         if (lane == 0) {
-          const int x = sg.x0 - 1;
-          const bool ok = x >= 0 && sg.y < g.ny;
-          sP[(warp + 1) * RS + HOFF - 1] = ok ? pnew_scalar(x, z) : T(0);
-          sTxh[warp] = ok ? Fx[(int64_t)z * g.nxy + (int64_t)sg.y * g.nx + x] : T(0);
+          sP[(warp + 1) * RS + HOFF - 1] = xz0 + beta * xp0;
+          sTxh[warp] = xf0;
         }
-        if (lane == 31) {
-          const int x = sg.x0 + TX;
-          const bool ok = x < g.nx && sg.y < g.ny;
-          sP[(warp + 1) * RS + HOFF + TX] = ok ? pnew_scalar(x, z) : T(0);
-        }
+        if (lane == 31) sP[(warp + 1) * RS + HOFF + TX] = xz0 + beta * xp0;
       } else {
-        T ph[CX];
-        pnew_at(z, ph);
+        T ph[CX], zv_n[CX], po_n[CX];
+        ld_raw(z + 1, zv_n, po_n);
+        T fyn[CX];
+        if (warp == kTY) ld_fy(z + 1, fyn);
+#pragma unroll
+        for (int c = 0; c < CX; ++c) ph[c] = zv2[c] + beta * po2[c];
         const int row = (warp == kTY) ? 0 : kTY + 1;
         sm_st<T, CX>(sP + row * RS + HOFF + lane * CX, ph);
         if (warp == kTY) {
-          T ty0[CX];
-          if (sg.nv > 0) ld_cells<T, CX, true>(Fy, iz, sg.nv, ty0);
-          else {
+          sm_st<T, CX>(sTy + lane * CX, F.fy);
 #pragma unroll
-            for (int c = 0; c < CX; ++c) ty0[c] = T(0);
-          }
-          sm_st<T, CX>(sTy + lane * CX, ty0);
+          for (int c = 0; c < CX; ++c) F.fy[c] = fyn[c];
+        }
+#pragma unroll
+        for (int c = 0; c < CX; ++c) {
+          zv2[c] = zv_n[c];
+          po2[c] = po_n[c];
         }
       }
       __syncthreads();
       if (sg.own) {
         T left = __shfl_up_sync(kFull, pc[CX - 1], 1);
         T right = __shfl_down_sync(kFull, pc[0], 1);
-        T txl = __shfl_up_sync(kFull, fx[CX - 1], 1);
+        T txl = __shfl_up_sync(kFull, F.fx[CX - 1], 1);
         if (lane == 0) {
           left = sP[(warp + 1) * RS + HOFF - 1];
           txl = sTxh[warp];
@@ -281,10 +340,11 @@ __device__ void sweep_A(const SolveArgs& a, const Sm<T>& sm, const T* zb, const 
           const T u = pc[c];
           const T xm = (c > 0) ? pc[(c > 0) ? c - 1 : 0] : left;
           const T xp = (c < CX - 1) ? pc[(c < CX - 1) ? c + 1 : 0] : right;
-          const T fxm = (c > 0) ? fx[(c > 0) ? c - 1 : 0] : txl;
-          const T v = stencil<T>(dxc[c] || dyc || dzc, u, dg[c], fxm, xm, !dxm[c], fx[c], xp, !dxp[c], fym[c],
-                                 ym[c], !dym, fy[c], yp[c], !dyp, tzm[c], pm[c], !dzm, fz[c], pn[c], !dzp);
-          la.add(valid, lb[c], v, sm.acc, d, warp);
+          const T fxm = (c > 0) ? F.fx[(c > 0) ? c - 1 : 0] : txl;
+          const T v = stencil<T>(dxc[c] || dyc || dzc, u, F.dg[c], fxm, xm, !dxm[c], F.fx[c], xp, !dxp[c],
+                                 fym[c], ym[c], !dym, F.fy[c], yp[c], !dyp, tzm[c], pm[c], !dzm, F.fz[c], pn[c],
+                                 !dzp);
+          la.add(valid, F.lb[c], v, sm.acc, d, warp);
           if (valid) gam += u * v;
         }
         st_cells<T, CX>(pnew, iz, sg.nv, pc);
@@ -292,8 +352,13 @@ __device__ void sweep_A(const SolveArgs& a, const Sm<T>& sm, const T* zb, const 
         for (int c = 0; c < CX; ++c) {
           pm[c] = pc[c];
           pc[c] = pn[c];
-          tzm[c] = fz[c];
+          pn[c] = zv2[c] + beta * po2[c];
+          tzm[c] = F.fz[c];
         }
+        F = F1;
+        xz0 = xz1;
+        xp0 = xp1;
+        xf0 = xf1;
       }
     }
     dgam += (double)gam;
@@ -314,8 +379,13 @@ __device__ void sweep_A(const SolveArgs& a, const Sm<T>& sm, const T* zb, const 
 
 // ---------------------------------------------------------------------------
 // Sweep B: u = p - Z y, w = A u, xhat += alpha p, r = diag z - alpha w,
-// z = r / diag, rho' = r . z, rr = r . r
+// z = r / diag, rho' = r . z, rr = r . r  (pipelined like sweep A)
 // ---------------------------------------------------------------------------
+template <typename T, int CX>
+struct FacesB {
+  T fx[CX], fy[CX], fz[CX], dg[CX], idg[CX], zo[CX], xo[CX];
+};
+
 template <typename T, int CX, bool WACC>
 __device__ void sweep_B(const SolveArgs& a, const Sm<T>& sm, const T* p, T* zb, T* xh, T alpha,
                         const T* __restrict__ Fx, const T* __restrict__ Fy, const T* __restrict__ Fz,
@@ -334,25 +404,76 @@ __device__ void sweep_B(const SolveArgs& a, const Sm<T>& sm, const T* p, T* zb, 
     const int z1 = (int)((int64_t)g.nz < (int64_t)z0 + (t1 - t) ? (int64_t)g.nz : (int64_t)z0 + (t1 - t));
     t += z1 - z0;
     const Seg sg = make_seg<TX>(a, ct, z0, z1, CX);
-    // u = p - y[label] at this lane's cells of plane zz; also returns p
-    auto u_at = [&](int zz, T(&u)[CX], T(&pv)[CX]) {
+    // raw p and labels of this lane's cells of plane zz
+    auto ld_raw = [&](int zz, T(&pv)[CX], int(&lb)[CX]) {
       if (zz < 0 || zz >= g.nz || sg.nv == 0) {
 #pragma unroll
-        for (int c = 0; c < CX; ++c) u[c] = pv[c] = T(0);
+        for (int c = 0; c < CX; ++c) {
+          pv[c] = T(0);
+          lb[c] = -1;
+        }
         return;
       }
-      int lb[CX];
       const int64_t i = (int64_t)zz * g.nxy + sg.rowbase;
       ld_cells<T, CX, false>(p, i, sg.nv, pv);
       ld_labels<CX>(a.label, i, sg.nv, lb);
+    };
+    auto mk_u = [&](const T(&pv)[CX], const int(&lb)[CX], T(&u)[CX]) {
 #pragma unroll
-      for (int c = 0; c < CX; ++c) u[c] = (c < sg.nv) ? pv[c] - Y[lb[c]] : T(0);
+      for (int c = 0; c < CX; ++c) u[c] = (lb[c] >= 0) ? pv[c] - Y[lb[c]] : T(0);
     };
-    auto u_scalar = [&](int x, int zz) -> T {
-      const int64_t i = (int64_t)zz * g.nxy + (int64_t)sg.y * g.nx + x;
-      return p[i] - Y[__ldg(a.label + i)];
+    auto ld_faces = [&](int zz, FacesB<T, CX>& f) {
+      if (zz < 0 || zz >= g.nz || sg.nv == 0) {
+#pragma unroll
+        for (int c = 0; c < CX; ++c) f.fx[c] = f.fy[c] = f.fz[c] = f.dg[c] = f.idg[c] = f.zo[c] = f.xo[c] = T(0);
+        return;
+      }
+      const int64_t i = (int64_t)zz * g.nxy + sg.rowbase;
+      ld_cells<T, CX, true>(Fx, i, sg.nv, f.fx);
+      ld_cells<T, CX, true>(Fy, i, sg.nv, f.fy);
+      ld_cells<T, CX, true>(Fz, i, sg.nv, f.fz);
+      if (sg.own) {
+        ld_cells<T, CX, false>(zb, i, sg.nv, f.zo);
+        ld_cells<T, CX, false>(xh, i, sg.nv, f.xo);
+      }
+      if constexpr (sizeof(T) == 8) {
+        ld_cells<T, CX, true>(a.diag64, i, sg.nv, f.dg);
+        ld_cells<T, CX, true>(a.invdiag64, i, sg.nv, f.idg);
+      } else {
+#pragma unroll
+        for (int c = 0; c < CX; ++c) f.dg[c] = f.idg[c] = T(0);
+      }
     };
-    T um[CX], uc[CX], un[CX], pcur[CX], pnx[CX], tzm[CX];
+    auto ld_fy = [&](int zz, T(&o)[CX]) {
+      if (zz < 0 || zz >= g.nz || sg.nv == 0) {
+#pragma unroll
+        for (int c = 0; c < CX; ++c) o[c] = T(0);
+        return;
+      }
+      ld_cells<T, CX, true>(Fy, (int64_t)zz * g.nxy + sg.rowbase, sg.nv, o);
+    };
+    const bool hl_ok = sg.own && lane == 0 && sg.x0 - 1 >= 0 && sg.y < g.ny;
+    const bool hr_ok = sg.own && lane == 31 && sg.x0 + TX < g.nx && sg.y < g.ny;
+    auto ld_xh = [&](int zz, T& px, int& lx, T& fxl) {
+      px = T(0);
+      lx = -1;
+      fxl = T(0);
+      if (zz < 0 || zz >= g.nz) return;
+      const int64_t row = (int64_t)zz * g.nxy + (int64_t)sg.y * g.nx;
+      if (hl_ok) {
+        px = p[row + sg.x0 - 1];
+        lx = __ldg(a.label + row + sg.x0 - 1);
+        fxl = __ldg(Fx + row + sg.x0 - 1);
+      } else if (hr_ok) {
+        px = p[row + sg.x0 + TX];
+        lx = __ldg(a.label + row + sg.x0 + TX);
+      }
+    };
+    T um[CX], uc[CX], un[CX], pcur[CX], pnx[CX], tzm[CX], p2[CX];
+    int l2[CX];
+    FacesB<T, CX> F, F1;
+    T xp0 = T(0), xf0 = T(0), xp1 = T(0), xf1 = T(0);
+    int xl0 = -1, xl1 = -1;
     bool dxc[CX], dxm[CX], dxp[CX];
 #pragma unroll
     for (int c = 0; c < CX; ++c) {
@@ -365,14 +486,23 @@ __device__ void sweep_B(const SolveArgs& a, const Sm<T>& sm, const T* p, T* zb, 
     const bool dym = dir_axis(sg.y - 1, g.ny, g.dlo_y, g.dhi_y);
     const bool dyp = dir_axis(sg.y + 1, g.ny, g.dlo_y, g.dhi_y);
     if (sg.own) {
-      T dummy[CX];
-      u_at(z0 - 1, um, dummy);
-      u_at(z0, uc, pcur);
-      if (z0 > 0 && sg.nv > 0) ld_cells<T, CX, true>(Fz, (int64_t)(z0 - 1) * g.nxy + sg.rowbase, sg.nv, tzm);
-      else {
+      T pv[CX];
+      int lb[CX];
+      ld_raw(z0 - 1, pv, lb);
+      mk_u(pv, lb, um);
+      ld_raw(z0, pcur, lb);
+      mk_u(pcur, lb, uc);
+      ld_raw(z0 + 1, pnx, lb);
+      mk_u(pnx, lb, un);
+      ld_faces(z0, F);
+      FacesB<T, CX> Fm;
+      ld_faces(z0 - 1, Fm);
 #pragma unroll
-        for (int c = 0; c < CX; ++c) tzm[c] = T(0);
-      }
+      for (int c = 0; c < CX; ++c) tzm[c] = Fm.fz[c];
+      ld_xh(z0, xp0, xl0, xf0);
+    } else {
+      ld_raw(z0, p2, l2);  // halo rows: plane z0
+      if (warp == kTY) ld_fy(z0, F.fy);
     }
     T rho = T(0), rr = T(0);
     for (int z = z0; z < z1; ++z) {
@@ -381,51 +511,42 @@ __device__ void sweep_B(const SolveArgs& a, const Sm<T>& sm, const T* p, T* zb, 
       T* sTy = sm.Ty + buf * (kTY + 1) * TX;
       T* sTxh = sm.Txh + buf * kTY;
       const int64_t iz = (int64_t)z * g.nxy + sg.rowbase;
-      T fx[CX], fy[CX], fz[CX], dg[CX] = {}, idg[CX] = {}, zo[CX], xo[CX];
       if (sg.own) {
-        u_at(z + 1, un, pnx);
-        ld_cells<T, CX, true>(Fx, iz, sg.nv, fx);
-        ld_cells<T, CX, true>(Fy, iz, sg.nv, fy);
-        ld_cells<T, CX, true>(Fz, iz, sg.nv, fz);
-        ld_cells<T, CX, false>(zb, iz, sg.nv, zo);
-        ld_cells<T, CX, false>(xh, iz, sg.nv, xo);
-        if constexpr (sizeof(T) == 8) {
-          ld_cells<T, CX, true>(a.diag64, iz, sg.nv, dg);
-          ld_cells<T, CX, true>(a.invdiag64, iz, sg.nv, idg);
-        }
+        ld_raw(z + 2, p2, l2);
+        ld_faces(z + 1, F1);
+        ld_xh(z + 1, xp1, xl1, xf1);
         sm_st<T, CX>(sP + (warp + 1) * RS + HOFF + lane * CX, uc);
-        sm_st<T, CX>(sTy + (warp + 1) * TX + lane * CX, fy);
+        sm_st<T, CX>(sTy + (warp + 1) * TX + lane * CX, F.fy);
         if (lane == 0) {
-          const int x = sg.x0 - 1;
-          const bool ok = x >= 0 && sg.y < g.ny;
-          sP[(warp + 1) * RS + HOFF - 1] = ok ? u_scalar(x, z) : T(0);
-          sTxh[warp] = ok ? Fx[(int64_t)z * g.nxy + (int64_t)sg.y * g.nx + x] : T(0);
+          sP[(warp + 1) * RS + HOFF - 1] = xl0 >= 0 ? xp0 - Y[xl0] : T(0);
+          sTxh[warp] = xf0;
         }
-        if (lane == 31) {
-          const int x = sg.x0 + TX;
-          const bool ok = x < g.nx && sg.y < g.ny;
-          sP[(warp + 1) * RS + HOFF + TX] = ok ? u_scalar(x, z) : T(0);
-        }
+        if (lane == 31) sP[(warp + 1) * RS + HOFF + TX] = xl0 >= 0 ? xp0 - Y[xl0] : T(0);
       } else {
-        T uh[CX], ph[CX];
-        u_at(z, uh, ph);
+        T uh[CX], pv[CX];
+        int lb[CX];
+        ld_raw(z + 1, pv, lb);
+        T fyn[CX];
+        if (warp == kTY) ld_fy(z + 1, fyn);
+        mk_u(p2, l2, uh);
         const int row = (warp == kTY) ? 0 : kTY + 1;
         sm_st<T, CX>(sP + row * RS + HOFF + lane * CX, uh);
         if (warp == kTY) {
-          T ty0[CX];
-          if (sg.nv > 0) ld_cells<T, CX, true>(Fy, iz, sg.nv, ty0);
-          else {
+          sm_st<T, CX>(sTy + lane * CX, F.fy);
 #pragma unroll
-            for (int c = 0; c < CX; ++c) ty0[c] = T(0);
-          }
-          sm_st<T, CX>(sTy + lane * CX, ty0);
+          for (int c = 0; c < CX; ++c) F.fy[c] = fyn[c];
+        }
+#pragma unroll
+        for (int c = 0; c < CX; ++c) {
+          p2[c] = pv[c];
+          l2[c] = lb[c];
         }
       }
       __syncthreads();
       if (sg.own) {
         T left = __shfl_up_sync(kFull, uc[CX - 1], 1);
         T right = __shfl_down_sync(kFull, uc[0], 1);
-        T txl = __shfl_up_sync(kFull, fx[CX - 1], 1);
+        T txl = __shfl_up_sync(kFull, F.fx[CX - 1], 1);
         if (lane == 0) {
           left = sP[(warp + 1) * RS + HOFF - 1];
           txl = sTxh[warp];
@@ -444,19 +565,19 @@ __device__ void sweep_B(const SolveArgs& a, const Sm<T>& sm, const T* p, T* zb, 
           const T u = uc[c];
           const T xm = (c > 0) ? uc[(c > 0) ? c - 1 : 0] : left;
           const T xp = (c < CX - 1) ? uc[(c < CX - 1) ? c + 1 : 0] : right;
-          const T fxm = (c > 0) ? fx[(c > 0) ? c - 1 : 0] : txl;
+          const T fxm = (c > 0) ? F.fx[(c > 0) ? c - 1 : 0] : txl;
           const bool dirc = dxc[c] || dyc || dzc;
           T dgi;
-          if constexpr (sizeof(T) == 8) dgi = dg[c];
-          else dgi = dirc ? T(1) : (((((tzm[c] + fym[c]) + fxm) + fx[c]) + fy[c]) + fz[c]);
-          const T w = stencil<T>(dirc, u, dgi, fxm, xm, !dxm[c], fx[c], xp, !dxp[c], fym[c], ym[c], !dym, fy[c],
-                                 yp[c], !dyp, tzm[c], um[c], !dzm, fz[c], un[c], !dzp);
-          const T r = dgi * zo[c] - alpha * w;
+          if constexpr (sizeof(T) == 8) dgi = F.dg[c];
+          else dgi = dirc ? T(1) : (((((tzm[c] + fym[c]) + fxm) + F.fx[c]) + F.fy[c]) + F.fz[c]);
+          const T w = stencil<T>(dirc, u, dgi, fxm, xm, !dxm[c], F.fx[c], xp, !dxp[c], fym[c], ym[c], !dym,
+                                 F.fy[c], yp[c], !dyp, tzm[c], um[c], !dzm, F.fz[c], un[c], !dzp);
+          const T r = dgi * F.zo[c] - alpha * w;
           T znew;
-          if constexpr (sizeof(T) == 8) znew = r * idg[c];
+          if constexpr (sizeof(T) == 8) znew = r * F.idg[c];
           else znew = __fdividef(r, dgi);  // FP32 inner: 2-ulp division
           zn[c] = znew;
-          xn[c] = xo[c] + alpha * pcur[c];
+          xn[c] = F.xo[c] + alpha * pcur[c];
           if (c < sg.nv) {
             rho += r * znew;
             rr += r * r;
@@ -464,13 +585,21 @@ __device__ void sweep_B(const SolveArgs& a, const Sm<T>& sm, const T* p, T* zb, 
         }
         st_cells<T, CX>(zb, iz, sg.nv, zn);
         st_cells<T, CX>(xh, iz, sg.nv, xn);
+        T u2[CX];
+        mk_u(p2, l2, u2);
 #pragma unroll
         for (int c = 0; c < CX; ++c) {
           um[c] = uc[c];
           uc[c] = un[c];
+          un[c] = u2[c];
           pcur[c] = pnx[c];
-          tzm[c] = fz[c];
+          pnx[c] = p2[c];
+          tzm[c] = F.fz[c];
         }
+        F = F1;
+        xp0 = xp1;
+        xl0 = xl1;
+        xf0 = xf1;
       }
     }
     drho += (double)rho;
@@ -506,7 +635,7 @@ __device__ __forceinline__ void solve_generic(const SolveArgs& a, unsigned char*
 }
 
 template <typename T, int CX, bool WACC>
-__global__ void __launch_bounds__(kThreads) k_solve(SolveArgs a) {
+__global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   solve_generic<T, CX, WACC>(a, smem_raw);
 }
@@ -516,7 +645,7 @@ __global__ void __launch_bounds__(kThreads) k_solve(SolveArgs a) {
 // team's own); teams never wait on each other, and a team leaves the kernel
 // as soon as its system is solved.
 template <typename T, int CX, bool WACC>
-__global__ void __launch_bounds__(kThreads) k_solve_batch(const SolveArgs* __restrict__ all,
+__global__ void __launch_bounds__(kThreads, 1) k_solve_batch(const SolveArgs* __restrict__ all,
                                                          const int* __restrict__ cta_sys) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ SolveArgs a;
@@ -765,11 +894,12 @@ void batch_free(BatchPlan* p) {
   p->d_cta = nullptr;
 }
 
-// Teams: system k gets a share of the CTAs proportional to n_k^expo (work per
-// iteration grows with n, the iteration count roughly with the side), at
-// least one CTA, at most one per plane tile and per partial-sum row.
-int batch_build(sld_system* sys, int count, const sld_options& o, int per_sm, double expo, int cx,
-                cudaStream_t stream, BatchPlan* p, std::string* msg) {
+// Teams: system k gets a share of the CTAs proportional to its weight --
+// n_k^expo by default (work per iteration grows with n, the iteration count
+// roughly with the side), or the caller's (measured work) -- at least one
+// CTA, at most one per plane tile and per partial-sum row.
+int batch_build(sld_system* sys, int count, const sld_options& o, int per_sm, double expo, const double* weights,
+                int cx, cudaStream_t stream, BatchPlan* p, std::string* msg) {
   sld_system s0 = sys[0];
   p->stream = stream;
   p->count = count;
@@ -809,7 +939,7 @@ int batch_build(sld_system* sys, int count, const sld_options& o, int per_sm, do
     a.nty = (a.g.ny + kTY - 1) / kTY;
     a.ntiles = (int64_t)a.ntx * a.nty * a.g.nz;
     cap[k] = (int)std::min<int64_t>(std::min<int64_t>(a.ntiles, sys[k]->part_rows), G);
-    w[k] = std::pow((double)a.g.n, expo);
+    w[k] = weights ? std::max(weights[k], 1e-30) : std::pow((double)a.g.n, expo);
     wsum += w[k];
   }
   int used = 0;
