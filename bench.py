@@ -37,6 +37,12 @@ WORKLOAD = "lognormal-layered 256x256x128, point source, 4x4x4 subdomains x 2 le
 BYTES_ITER_FP32 = 60   # A: z, p_old, 3 faces, label, p_new  B: p, label, 3 faces, z r/w, xhat r/w
 BYTES_ITER_FP64 = 140  # same vectors and faces in FP64 + diag (A, B) and 1/diag (B)
 BYTES_OUTER = 152      # O1: x, xhat, b, faces, diag, label, r'  O2: r', label, faces, diag, x r/w, xhat r/w, 1/diag, z, p0, p1
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) over algorithmic
+# bytes of one launch of k_solve_tma<float, float, 16, 3, true>, from an ncu
+# capture of a 300-iteration launch on this workload (167.1 GB / 153.5 GB);
+# the traffic of a full launch is this ratio times its algorithmic bytes.
+# Must be re-measured (or set to None) whenever that kernel changes.
+TRAFFIC_RATIO_FP32 = 1.088
 
 
 def _peaks():
@@ -200,6 +206,32 @@ def run_reference(args):
     return 0
 
 
+def profile_solve(args):
+    """One solve of the bench workload (optionally on another grid and with
+    an iteration cap), so that a profiler captures exactly one launch of the
+    persistent solve kernel."""
+    import torch
+    from paper_1510_02148_gb300 import _build, sld, workloads as W
+    _build.build()
+    sld.load()
+    shape = tuple(args.shape) if args.shape else (256, 256, 128)
+    P = W.lognormal_point_source(*shape, seed=1)
+    s = sld.System(torch.from_numpy(P.K.reshape(-1)).cuda(), torch.from_numpy(P.q.reshape(-1)).cuda(),
+                   P.bc_type, P.bc_value, shape=P.shape)
+    s.make_labels(P.S, P.tau, P.L)
+    s.build_deflation(P.d)
+    x = torch.empty(P.n, dtype=torch.float64, device="cuda")
+    prec = {"fp64": sld.FP64, "fp32_ir": sld.FP32_IR, "bf16": sld.BF16COEF_IR}[args.profile_solve]
+    kw = {"maxiter": args.maxiter} if args.maxiter > 0 else {}
+    _, info = s.solve(x=x, precision=prec, raise_on_error=False, **kw)
+    torch.cuda.synchronize()
+    s.close()
+    print(json.dumps({"profile_solve": args.profile_solve, "shape": shape, "status": info.status,
+                      "iterations": info.iterations, "outer_steps": info.outer_steps, "solve_ms": info.solve_ms,
+                      "kernel_path": info.kernel_path}), flush=True)
+    return 0 if info.status in (sld.OK, sld.ERR_NOT_CONVERGED) else 1
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -209,9 +241,15 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--profile-solve", choices=["fp64", "fp32_ir", "bf16"], default=None,
+                    help="set up the workload and run one solve (for profiler captures); no timing line")
+    ap.add_argument("--maxiter", type=int, default=0, help="with --profile-solve: inner iteration cap")
+    ap.add_argument("--shape", type=int, nargs=3, default=None, help="with --profile-solve: grid nx ny nz")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_solve:
+        return profile_solve(args)
 
     import torch
     from paper_1510_02148_gb300 import _build, sld, workloads as W
@@ -306,7 +344,8 @@ def main():
         "hbm_gbs": achieved,
         "setup_ms": setup_ms,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": achieved / hbm_peak, "traffic": None,
+                     "frac": achieved / hbm_peak,
+                     "traffic": (TRAFFIC_RATIO_FP32 * alg_bytes if TRAFFIC_RATIO_FP32 else None),
                      "kernel": "k_solve_tma<float,16,3,true> (persistent, cooperative)", "peak_kind": peak_kind},
         "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(Kh.numel() * 8 + qh.numel() * 8),
                 "d2h_bytes_per_step": int(xh.numel() * 8),
