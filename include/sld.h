@@ -65,6 +65,9 @@ enum { SLD_BC_NOFLOW = 0, SLD_BC_DIRICHLET = 1 };
 /* Inner precision of the solve. */
 enum { SLD_FP64 = 0, SLD_FP32_IR = 1, SLD_BF16COEF_IR = 2 };
 
+/* Element type of the extra dense deflation vectors given to sld_build_deflation. */
+enum { SLD_ZEXTRA_F64 = 0, SLD_ZEXTRA_F32 = 1 };
+
 typedef struct {
   int nx, ny, nz; /* cells per axis, each >= 1; unit cell size */
 } sld_grid;
@@ -140,15 +143,31 @@ sld_status sld_make_labels(sld_system s, int Sx, int Sy, int Sz, const double* t
  * Deflation space Z = [Z_lab, Z_extra] (Section 3.1, Def. 3.1): Z_lab has d
  * indicator columns (column labels[i] is 1 in row i), Z_extra k dense columns.
  * Builds E = Z^T A Z (eq. (E)) on the device, pins E_cc = 1 for an empty
- * column c, factors E = L L^T (FP64 Cholesky) and forms E^{-1}.
+ * label column c, factors E = L L^T (FP64 Cholesky) and forms E^{-1}.
  *   labels: n int32 in [0, d), or NULL to use those of sld_make_labels.
- *   d: 1 .. 65535.
- *   Zextra, k, zextra_dtype: reserved for extra dense vectors; pass NULL, 0, 0.
- * Errors: SLD_ERR_INVALID_ARG (label out of range), SLD_ERR_COARSE_SINGULAR
- * (a pivot <= 0), SLD_ERR_TIMEOUT, SLD_ERR_CUDA.
+ *   d: 1 .. 4096.
+ *   Zextra: n x k values, row-major (the k values of cell i contiguous), host
+ *     or device memory, FP64 or FP32 as zextra_dtype says (SLD_ZEXTRA_F64,
+ *     SLD_ZEXTRA_F32); NULL when k == 0.  k: 0 .. 8.  The values are rounded
+ *     to FP32 and those rounded vectors are the extra columns.  The solver
+ *     keeps them with W = A Z_extra (FP64 and FP32): k * 20 bytes per cell.
+ *     The Cholesky factorisation bounds the extra columns' pivots relative
+ *     to their diagonal (1e-10); if that fails (a column numerically in the
+ *     span of the others), the extra columns are dropped and the label
+ *     deflation alone is built -- sld_deflation_info reports k_used = 0.
+ *     Extra columns need the TMA solve path (nx % 8 == 0), SLD_FP64 or
+ *     SLD_FP32_IR, and a single (not batched) solve.
+ * Errors: SLD_ERR_INVALID_ARG (label out of range, k out of range, Zextra
+ * NULL with k > 0 or non-finite), SLD_ERR_COARSE_SINGULAR (a label pivot
+ * <= 0), SLD_ERR_TIMEOUT, SLD_ERR_CUDA.
  */
 sld_status sld_build_deflation(sld_system s, const int32_t* labels, int d, const void* Zextra,
                                int k, int zextra_dtype);
+
+/* The deflation last built: d label columns, the k extra columns asked
+ * for, and k_used (k, or 0 if they were dropped).  Any pointer may be NULL.
+ * Errors: SLD_ERR_STATE (no deflation built). */
+sld_status sld_deflation_info(sld_system s, int* d, int* k_requested, int* k_used);
 
 /*
  * Solve A x = b by SLD-deflated Jacobi-PCG (the CG form of the deflated
@@ -235,7 +254,8 @@ sld_status sld_apply_A(sld_system s, const double* x, double* y);
 /* out = Z^T v (d values; the segmented sum over labels), FP64. */
 sld_status sld_restrict(sld_system s, const double* v, double* out);
 
-/* Copy out E (d*d, row-major) and E^{-1} (d*d); either may be NULL. */
+/* Copy out E (D*D, row-major, D = d + k_used: label columns first, then the
+ * extra columns) and E^{-1} (D*D); either may be NULL. */
 sld_status sld_get_coarse(sld_system s, double* E, double* Einv);
 
 /* ---------------------------------------------------------------------- */

@@ -61,6 +61,11 @@ void dfree(void* p) {
   if (p) cudaFree(p);
 }
 
+// Relative Cholesky pivot bound for the extra dense columns: a pivot below
+// this fraction of its diagonal means the column is numerically in the span
+// of the others (E would be near-singular), and the extra columns are dropped.
+constexpr double kLearnedPivotTol = 1e-10;
+
 __global__ void k_count_bad_K(int64_t n, const double* __restrict__ K, unsigned long long* bad) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) {
@@ -89,10 +94,10 @@ sld_status ensure_workspace(sld_system s, bool need_fp32, bool need_bf16) {
   }
   if (s->part_rows == 0 || !s->part) {
     s->part_rows = s->nsm * 8;
-    const int pstride = (sld::kMaxD + sld::kPartScalars + 3) / 4 * 4;
+    const int pstride = (sld::kMaxD + sld::kMaxL + sld::kPartScalars + 3) / 4 * 4;
     if ((e = dalloc(&s->part, (size_t)s->part_rows * pstride)) != cudaSuccess) return cuda_fail(e, "alloc partials");
-    if ((e = dalloc(&s->s_glob, sld::kMaxD)) != cudaSuccess) return cuda_fail(e, "alloc s");
-    if ((e = dalloc(&s->y_glob, sld::kMaxD)) != cudaSuccess) return cuda_fail(e, "alloc y");
+    if ((e = dalloc(&s->s_glob, sld::kMaxD + sld::kMaxL)) != cudaSuccess) return cuda_fail(e, "alloc s");
+    if ((e = dalloc(&s->y_glob, sld::kMaxD + sld::kMaxL)) != cudaSuccess) return cuda_fail(e, "alloc y");
   }
   if (need_fp32 && !s->Tx32) {
     if ((e = dalloc(&s->Tx32, n)) != cudaSuccess) return cuda_fail(e, "alloc Tx32");
@@ -124,7 +129,7 @@ sld_status ensure_workspace(sld_system s, bool need_fp32, bool need_bf16) {
     dfree(wide);
     if (e != cudaSuccess) return cuda_fail(e, "bf16 coarse matrix");
     std::string msg;
-    const int st = sld::coarse_factor(s, s->E16, s->Einv16, 2.0, &msg);
+    const int st = sld::coarse_factor(s, s->d, s->E16, s->Einv16, 2.0, &msg);
     if (st != SLD_OK) return fail((sld_status)st, "bf16 coarse matrix: " + msg);
     s->bf16_ready = true;
   }
@@ -284,9 +289,11 @@ sld_status sld_make_labels(sld_system s, int Sx, int Sy, int Sz, const double* t
 sld_status sld_build_deflation(sld_system s, const int32_t* labels, int d, const void* Zextra, int k,
                                int zextra_dtype) {
   g_last_error.clear();
-  (void)zextra_dtype;
   if (!s) return fail(SLD_ERR_INVALID_ARG, "handle is NULL");
-  if (Zextra || k != 0) return fail(SLD_ERR_INVALID_ARG, "extra dense vectors are not supported by this entry point");
+  if (k < 0 || k > sld::kMaxL) return fail(SLD_ERR_INVALID_ARG, "k must be in [0, " + std::to_string(sld::kMaxL) + "]");
+  if ((k > 0) != (Zextra != nullptr)) return fail(SLD_ERR_INVALID_ARG, "Zextra must be given exactly when k > 0");
+  if (k > 0 && zextra_dtype != SLD_ZEXTRA_F64 && zextra_dtype != SLD_ZEXTRA_F32)
+    return fail(SLD_ERR_INVALID_ARG, "zextra_dtype must be SLD_ZEXTRA_F64 or SLD_ZEXTRA_F32");
   if (d < 1 || d > sld::kMaxD) return fail(SLD_ERR_INVALID_ARG, "d must be in [1, " + std::to_string(sld::kMaxD) + "]");
   cudaError_t e;
   if (labels) {
@@ -297,14 +304,15 @@ sld_status sld_build_deflation(sld_system s, const int32_t* labels, int d, const
   } else if (!s->label || s->have_labels_d == 0) {
     return fail(SLD_ERR_STATE, "no labels: pass them or call sld_make_labels first");
   }
-  if (d != s->d) {
-    dfree(s->E);
-    dfree(s->Einv);
-    s->E = s->Einv = nullptr;
-    if ((e = dalloc(&s->E, (size_t)d * d)) != cudaSuccess) return cuda_fail(e, "alloc E");
-    if ((e = dalloc(&s->Einv, (size_t)d * d)) != cudaSuccess) return cuda_fail(e, "alloc Einv");
-  }
+  const int D = d + k;
+  dfree(s->E);
+  dfree(s->Einv);
+  s->E = s->Einv = nullptr;
+  if ((e = dalloc(&s->E, (size_t)D * D)) != cudaSuccess) return cuda_fail(e, "alloc E");
+  if ((e = dalloc(&s->Einv, (size_t)D * D)) != cudaSuccess) return cuda_fail(e, "alloc Einv");
   s->d = d;
+  s->kL = 0;
+  s->kL_requested = k;
   s->deflation_ready = false;
   s->bf16_ready = false;
   int bad = 0;
@@ -314,9 +322,71 @@ sld_status sld_build_deflation(sld_system s, const int32_t* labels, int d, const
   if (!s->label16 && (e = dalloc(&s->label16, s->g.n)) != cudaSuccess) return cuda_fail(e, "alloc labels16");
   if ((e = sld::launch_labels16(s)) != cudaSuccess) return cuda_fail(e, "labels16");
   std::string msg;
-  const int st = sld::coarse_factor(s, s->E, s->Einv, 2.0, &msg);
+  if (k > 0) {
+    // Z = [Z_lab, Z_L]: E with the extra blocks, factored with a relative
+    // pivot bound on the extra columns; if that fails the extra columns are
+    // dropped and the plain label deflation is built instead.
+    const int64_t n = s->g.n;
+    if (!s->ZL32) {
+      if ((e = dalloc(&s->ZL32, (size_t)n * sld::kMaxL)) != cudaSuccess) return cuda_fail(e, "alloc Z_L");
+      if ((e = dalloc(&s->WL64, (size_t)n * sld::kMaxL)) != cudaSuccess) return cuda_fail(e, "alloc W_L");
+      if ((e = dalloc(&s->WL32, (size_t)n * sld::kMaxL)) != cudaSuccess) return cuda_fail(e, "alloc W_L32");
+    }
+    const size_t zbytes = (zextra_dtype == SLD_ZEXTRA_F32 ? 4 : 8) * (size_t)n * k;
+    const void* zsrc = Zextra;
+    void* staged = nullptr;
+    if (!is_device_ptr(Zextra)) {
+      if ((e = cudaMalloc(&staged, zbytes)) != cudaSuccess) return cuda_fail(e, "alloc Zextra staging");
+      if ((e = cudaMemcpyAsync(staged, Zextra, zbytes, cudaMemcpyHostToDevice, s->stream)) != cudaSuccess) {
+        cudaFree(staged);
+        return cuda_fail(e, "copy Zextra");
+      }
+      zsrc = staged;
+    }
+    double* Ef = nullptr;
+    if ((e = dalloc(&Ef, (size_t)D * D)) != cudaSuccess) {
+      if (staged) cudaFree(staged);
+      return cuda_fail(e, "alloc E");
+    }
+    int zbad = 0;
+    e = sld::launch_learned_setup(s, zsrc, k, zextra_dtype == SLD_ZEXTRA_F32, s->E, Ef, &zbad);
+    if (staged) cudaFree(staged);
+    if (e != cudaSuccess) {
+      dfree(Ef);
+      return cuda_fail(e, "extra vectors");
+    }
+    if (zbad) {
+      dfree(Ef);
+      return fail(SLD_ERR_INVALID_ARG, "Zextra holds a non-finite value");
+    }
+    s->kL = k;
+    const int st = sld::coarse_factor(s, D, Ef, s->Einv, 2.0, &msg, d, kLearnedPivotTol);
+    if (st == SLD_OK) {
+      cudaMemcpyAsync(s->E, Ef, sizeof(double) * D * D, cudaMemcpyDeviceToDevice, s->stream);
+      e = cudaStreamSynchronize(s->stream);
+      dfree(Ef);
+      if (e != cudaSuccess) return cuda_fail(e, "copy E");
+      s->deflation_ready = true;
+      return SLD_OK;
+    }
+    dfree(Ef);
+    if (st != SLD_ERR_COARSE_SINGULAR) return fail((sld_status)st, msg);
+    s->kL = 0;  // fall back to the label columns alone
+    msg.clear();
+  }
+  const int st = sld::coarse_factor(s, d, s->E, s->Einv, 2.0, &msg);
   if (st != SLD_OK) return fail((sld_status)st, msg);
   s->deflation_ready = true;
+  return SLD_OK;
+}
+
+sld_status sld_deflation_info(sld_system s, int* d, int* k_requested, int* k_used) {
+  g_last_error.clear();
+  if (!s) return fail(SLD_ERR_INVALID_ARG, "handle is NULL");
+  if (!s->deflation_ready) return fail(SLD_ERR_STATE, "no deflation built");
+  if (d) *d = s->d;
+  if (k_requested) *k_requested = s->kL_requested;
+  if (k_used) *k_used = s->kL;
   return SLD_OK;
 }
 
@@ -371,7 +441,7 @@ void sld_destroy(sld_system s) {
   if (s->stream) cudaStreamSynchronize(s->stream);
   void* ptrs[] = {s->K, s->Tx, s->Ty, s->Tz, s->diag, s->invdiag, s->b, s->Tx32, s->Ty32, s->Tz32,
                   s->Tx16, s->Ty16, s->Tz16, s->invd16, s->E16, s->Einv16,
-                  s->label, s->label16, s->E, s->Einv, s->x, s->r64, s->bwork, s->z, s->p0, s->p1, s->xh,
+                  s->label, s->label16, s->E, s->Einv, s->ZL32, s->WL64, s->WL32, s->x, s->r64, s->bwork, s->z, s->p0, s->p1, s->xh,
                   s->part, s->s_glob, s->y_glob, s->out, s->bar, s->status};
   for (void* p : ptrs) dfree(p);
   if (s->ev0) cudaEventDestroy(s->ev0);
@@ -442,7 +512,7 @@ sld_status sld_get_coarse(sld_system s, double* E, double* Einv) {
   g_last_error.clear();
   if (!s) return fail(SLD_ERR_INVALID_ARG, "handle is NULL");
   if (!s->E) return fail(SLD_ERR_STATE, "no deflation built");
-  const size_t bytes = sizeof(double) * s->d * s->d;
+  const size_t bytes = sizeof(double) * s->dk() * s->dk();
   cudaError_t e = cudaSuccess;
   if (E) e = cudaMemcpyAsync(E, s->E, bytes, kind_out(E), s->stream);
   if (e == cudaSuccess && Einv) e = cudaMemcpyAsync(Einv, s->Einv, bytes, kind_out(Einv), s->stream);
@@ -515,6 +585,7 @@ sld_status sld_batch_create(sld_system* systems, int count, const sld_options* o
     sld_system s = systems[k];
     if (!s) return fail(SLD_ERR_INVALID_ARG, "a system is NULL");
     if (!s->deflation_ready) return fail(SLD_ERR_STATE, "every system needs sld_build_deflation first");
+    if (s->kL > 0) return fail(SLD_ERR_INVALID_ARG, "extra dense deflation columns are not supported in a batched solve");
     if (s->device != systems[0]->device) return fail(SLD_ERR_INVALID_ARG, "systems on different devices");
     for (int j = 0; j < k; ++j)
       if (systems[j] == s) return fail(SLD_ERR_INVALID_ARG, "a system appears twice");

@@ -19,7 +19,8 @@ constexpr int kWarps = kTY + 2;         // + two halo-row warps
 constexpr int kThreads = kWarps * 32;   // 320
 constexpr int kMaxD = 4096;             // largest d (labels) the kernels take
 constexpr int kWarpAccMaxD = 256;       // per-warp label accumulators up to this d
-constexpr int kPartScalars = 8;         // scalar slots after the d label sums
+constexpr int kPartScalars = 8;         // scalar slots after the dk coarse sums
+constexpr int kMaxL = 8;                // extra dense deflation vectors (slots per cell)
 
 struct SyncArgs {
   unsigned* count;                // arrival counter of the team, zeroed before the launch
@@ -43,13 +44,20 @@ struct SolveArgs {
   int cx;                 // cells per lane in x (1 or 4)
   int ntx, nty;           // column tiles in x and y
   int64_t ntiles;         // ntx * nty * nz plane-tiles
-  int d;
+  int d;                  // label columns of Z
+  int kL;                 // extra dense columns of Z (0 .. kMaxL)
+  int dk;                 // coarse dimension d + kL
   const int32_t* label;
   const uint16_t* label16;  // the same labels as 16-bit (streamed by the TMA sweeps)
   int lab_L;                // labels are subdomain * lab_L + class (1..4), or 0: any labels
   const double* Einv;     // d x d, E = Z^T A Z of the FP64 operator (refinement steps)
   const double* Einv_inner;  // the inverse used by the inner iterations (E of their operator)
   const float* invdi;     // BF16 form: FP32 inverse diagonal of the quantized operator
+  // extra dense columns: Z_L (FP32 values, kMaxL per cell), W_L = A Z_L in
+  // FP64 (refinement steps) and in the inner precision (double or float)
+  const float* ZL32;
+  const double* WL64;
+  const void* WLi;
   // FP64 operator
   const double *Tx64, *Ty64, *Tz64, *diag64, *invdiag64, *b;
   double* x;              // solution (FP64)
@@ -60,8 +68,8 @@ struct SolveArgs {
   // reductions
   double* part;           // [grid][pstride]
   int pstride;
-  double* s_glob;         // d
-  double* y_glob;         // d
+  double* s_glob;         // dk
+  double* y_glob;         // dk
   double* out;            // results: see kOut*
   SyncArgs sy;
   double tol, inner_tol;
@@ -97,8 +105,14 @@ struct sld_system_s {
   uint16_t* label16 = nullptr;
   int d = 0, have_labels_d = 0;
   int labels_L = 0;  // L of labels made by sld_make_labels (0 after user labels)
-  double *E = nullptr, *Einv = nullptr;
+  double *E = nullptr, *Einv = nullptr;  // dk x dk, dk = d + kL
   bool deflation_ready = false;
+  // extra dense deflation vectors (kMaxL slots per cell, zero past kL)
+  int kL = 0, kL_requested = 0;
+  float* ZL32 = nullptr;   // Z_L, FP32
+  double* WL64 = nullptr;  // A Z_L, FP64
+  float* WL32 = nullptr;   // A Z_L rounded to FP32
+  int dk() const { return d + kL; }
   // solve work space (lazily made)
   double *x = nullptr, *r64 = nullptr, *bwork = nullptr;
   void *z = nullptr, *p0 = nullptr, *p1 = nullptr, *xh = nullptr;  // sized for FP64
@@ -115,8 +129,15 @@ cudaError_t launch_assemble(sld_system s, const double* q);
 cudaError_t launch_labels(sld_system s, int Sx, int Sy, int Sz, const double* tau, int L);
 cudaError_t launch_coarse_E(sld_system s, const double* Tx, const double* Ty, const double* Tz, double* E,
                             int* bad_label);
-int coarse_factor(sld_system s, const double* E, double* Einv, double timeout_s,
-                  std::string* msg);  // returns sld_status
+// E (dim x dim) = L L^T and Einv.  Pivots k >= rel_from must also exceed
+// rel_tol times their original diagonal (else SLD_ERR_COARSE_SINGULAR).
+int coarse_factor(sld_system s, int dim, const double* E, double* Einv, double timeout_s, std::string* msg,
+                  int rel_from = 1 << 30, double rel_tol = 0.0);  // returns sld_status
+// Z_L from n x k user values (row-major, FP64 or FP32), W_L = A Z_L, and the
+// blocks Z_lab^T W_L (d x k) and Z_L^T W_L (k x k) written into Efull
+// (dk x dk) next to the label block E (d x d).  *bad: non-finite inputs.
+cudaError_t launch_learned_setup(sld_system s, const void* Zextra_dev, int k, int f32, const double* E,
+                                 double* Efull, int* bad);
 cudaError_t launch_quantize_bf16(sld_system s);
 cudaError_t launch_widen_bf16(sld_system s, double* Tx, double* Ty, double* Tz);
 cudaError_t launch_quantize_fp32(sld_system s);
@@ -128,6 +149,8 @@ cudaError_t launch_residual(sld_system s, const double* b, const double* x, doub
 // sld_solve_tma.cu
 bool tma_eligible(const Geo& g);
 int launch_solve_tma(sld_system s, SolveArgs& a, const sld_options& o, float* ms, std::string* msg);
+// sld_solve_tma_learned.cu (extra dense deflation columns)
+int launch_solve_tma_learned(sld_system s, SolveArgs& a, const sld_options& o, float* ms, std::string* msg);
 // sld_api.cu: the thread-local message returned by sld_last_error()
 void set_last_error(const std::string& msg);
 // sld_solve.cu

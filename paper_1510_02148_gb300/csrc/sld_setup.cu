@@ -172,13 +172,17 @@ __global__ void k_pin_empty(int d, const unsigned long long* __restrict__ count,
 // updates the owned rows of the trailing lower triangle; one bounded grid
 // barrier per column.  A pivot <= 0 (E not SPD) sets SLD_ERR_COARSE_SINGULAR;
 // every CTA reads the same pivot, so all of them stop at the same step.
-__global__ void k_cholesky(int d, double* __restrict__ A, double* __restrict__ Lm, SyncArgs sy) {
+// Pivots k >= rel_from must also exceed rel_tol times the original diagonal
+// E0_kk: a column that is (nearly) a combination of the earlier ones fails.
+__global__ void k_cholesky(int d, double* __restrict__ A, double* __restrict__ Lm, SyncArgs sy,
+                           const double* __restrict__ E0, int rel_from, double rel_tol) {
   extern __shared__ double sc[];
   unsigned epoch = 0;
   const int G = gridDim.x;
   for (int k = 0; k < d; ++k) {
     const double akk = A[(int64_t)k * d + k];
-    if (!(akk > 0.0) || !isfinite(akk)) {
+    const bool rel_bad = k >= rel_from && !(akk > rel_tol * E0[(int64_t)k * d + k]);
+    if (!(akk > 0.0) || !isfinite(akk) || rel_bad) {
       if (threadIdx.x == 0) atomicCAS(sy.status, 0, (int)SLD_ERR_COARSE_SINGULAR);
       return;
     }
@@ -241,6 +245,124 @@ __global__ void k_wtw(int d, const double* __restrict__ W, double* __restrict__ 
     __syncthreads();
   }
   if (i < d && j < d) Einv[(int64_t)i * d + j] = acc;
+}
+
+// ---------------------------------------------------------------------------
+// Extra dense deflation vectors Z_L (k <= kMaxL columns appended to the label
+// columns, Z = [Z_lab, Z_L]; Section 3.1, Def. 3.1 holds for any full-rank
+// Z).  Stored cell-major with kMaxL FP32 slots per cell (zero past k): the
+// FP32-rounded values are the vectors deflated with.  W_L = A Z_L in FP64
+// (refinement steps, coarse matrix) and rounded to FP32 (inner iterations).
+// ---------------------------------------------------------------------------
+__global__ void k_learned_pack(int64_t n, int k, const void* __restrict__ src, int f32, float* __restrict__ ZL,
+                               int* __restrict__ bad) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float v[kMaxL];
+#pragma unroll
+  for (int j = 0; j < kMaxL; ++j) {
+    float t = 0.0f;
+    if (j < k) t = f32 ? static_cast<const float*>(src)[i * k + j] : (float)static_cast<const double*>(src)[i * k + j];
+    if (!isfinite(t)) {
+      atomicExch(bad, 1);
+      t = 0.0f;
+    }
+    v[j] = t;
+  }
+  float4* o = reinterpret_cast<float4*>(ZL + i * kMaxL);
+  o[0] = make_float4(v[0], v[1], v[2], v[3]);
+  o[1] = make_float4(v[4], v[5], v[6], v[7]);
+}
+
+// W_L = A Z_L column by column, the operator of k_apply_A.
+__global__ void k_learned_W(Geo g, const double* __restrict__ Tx, const double* __restrict__ Ty,
+                            const double* __restrict__ Tz, const double* __restrict__ diag,
+                            const float* __restrict__ ZL, double* __restrict__ W64, float* __restrict__ W32) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= g.n) return;
+  const int ix = (int)(i % g.nx), iy = (int)((i / g.nx) % g.ny), iz = (int)(i / g.nxy);
+  const bool dirc = dir_axis(ix, g.nx, g.dlo_x, g.dhi_x) || dir_axis(iy, g.ny, g.dlo_y, g.dhi_y) ||
+                    dir_axis(iz, g.nz, g.dlo_z, g.dhi_z);
+  double w[kMaxL];
+  const double dg = dirc ? 1.0 : diag[i];
+#pragma unroll
+  for (int j = 0; j < kMaxL; ++j) w[j] = dg * (double)ZL[i * kMaxL + j];
+  if (!dirc) {
+    auto sub = [&](int64_t jn, double t) {
+#pragma unroll
+      for (int j = 0; j < kMaxL; ++j) w[j] -= t * (double)ZL[jn * kMaxL + j];
+    };
+    if (ix > 0 && !dir_axis(ix - 1, g.nx, g.dlo_x, g.dhi_x)) sub(i - 1, Tx[i - 1]);
+    if (ix + 1 < g.nx && !dir_axis(ix + 1, g.nx, g.dlo_x, g.dhi_x)) sub(i + 1, Tx[i]);
+    if (iy > 0 && !dir_axis(iy - 1, g.ny, g.dlo_y, g.dhi_y)) sub(i - g.nx, Ty[i - g.nx]);
+    if (iy + 1 < g.ny && !dir_axis(iy + 1, g.ny, g.dlo_y, g.dhi_y)) sub(i + g.nx, Ty[i]);
+    if (iz > 0 && !dir_axis(iz - 1, g.nz, g.dlo_z, g.dhi_z)) sub(i - g.nxy, Tz[i - g.nxy]);
+    if (iz + 1 < g.nz && !dir_axis(iz + 1, g.nz, g.dlo_z, g.dhi_z)) sub(i + g.nxy, Tz[i]);
+  }
+#pragma unroll
+  for (int j = 0; j < kMaxL; ++j) {
+    W64[i * kMaxL + j] = w[j];
+    W32[i * kMaxL + j] = (float)w[j];
+  }
+}
+
+// Z_lab^T W_L: ESL[a * kMaxL + j] = sum over cells with label a of W_ij.  A
+// warp whose 32 cells share one label adds its warp sum once.
+__global__ void k_learned_ESL(int64_t n, const int32_t* __restrict__ label, const double* __restrict__ W64,
+                              double* __restrict__ ESL) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t nround = (n + stride - 1) / stride;
+  const int lane = threadIdx.x & 31;
+  for (int64_t r = 0; r < nround; ++r) {
+    const int64_t i = r * stride + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool ok = i < n;
+    const int l = ok ? label[i] : -1;
+    const int l0 = __shfl_sync(kFull, l, 0);
+    const bool uniform = __all_sync(kFull, l == l0) && l0 >= 0;
+#pragma unroll
+    for (int j = 0; j < kMaxL; ++j) {
+      const double v = ok ? W64[i * kMaxL + j] : 0.0;
+      if (uniform) {
+        const double t = warp_sum(v);
+        if (lane == 0) atomicAdd(&ESL[(int64_t)l0 * kMaxL + j], t);
+      } else if (ok) {
+        atomicAdd(&ESL[(int64_t)l * kMaxL + j], v);
+      }
+    }
+  }
+}
+
+// Z_L^T W_L: one CTA per entry (j, m), fixed-order block sum.
+__global__ void k_learned_ELL(int64_t n, const float* __restrict__ ZL, const double* __restrict__ W64,
+                              double* __restrict__ ELL) {
+  __shared__ double red[32];
+  const int j = blockIdx.x / kMaxL, m = blockIdx.x % kMaxL;
+  double t = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) t += (double)ZL[i * kMaxL + j] * W64[i * kMaxL + m];
+  t = warp_sum(t);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double u = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) u += red[w];
+    ELL[j * kMaxL + m] = u;
+  }
+}
+
+// Efull (D x D, D = d + k) = [[E, ESL], [ESL^T, ELL]] restricted to k columns;
+// the label block is E (d x d).  ELL is symmetrised, (ELL + ELL^T) / 2.
+__global__ void k_learned_Efull(int d, int k, const double* __restrict__ E, const double* __restrict__ ESL,
+                                const double* __restrict__ ELL, double* __restrict__ Ef) {
+  const int D = d + k;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)D * D) return;
+  const int r = (int)(t / D), c = (int)(t % D);
+  double v;
+  if (r < d && c < d) v = E[(int64_t)r * d + c];
+  else if (r < d) v = ESL[(int64_t)r * kMaxL + (c - d)];
+  else if (c < d) v = ESL[(int64_t)c * kMaxL + (r - d)];
+  else v = 0.5 * (ELL[(r - d) * kMaxL + (c - d)] + ELL[(c - d) * kMaxL + (r - d)]);
+  Ef[t] = v;
 }
 
 template <typename Tout>
@@ -433,8 +555,9 @@ cudaError_t launch_coarse_E(sld_system s, const double* Tx, const double* Ty, co
   return e;
 }
 
-int coarse_factor(sld_system s, const double* E, double* Einv, double timeout_s, std::string* msg) {
-  const int d = s->d;
+int coarse_factor(sld_system s, int dim, const double* E, double* Einv, double timeout_s, std::string* msg,
+                  int rel_from, double rel_tol) {
+  const int d = dim;
   double *A = nullptr, *Lm = nullptr, *W = nullptr;
   unsigned* bar = nullptr;
   int* st = nullptr;
@@ -464,7 +587,7 @@ int coarse_factor(sld_system s, const double* E, double* Einv, double timeout_s,
   if (per < 1) G = 1;
   sy.cta0 = 0;
   sy.ncta = G;
-  void* args[] = {(void*)&d, (void*)&A, (void*)&Lm, (void*)&sy};
+  void* args[] = {(void*)&d, (void*)&A, (void*)&Lm, (void*)&sy, (void*)&E, (void*)&rel_from, (void*)&rel_tol};
   e = cudaLaunchCooperativeKernel((void*)k_cholesky, dim3(G), dim3(256), args, smem, s->stream);
   int hst = 0;
   if (e == cudaSuccess) {
@@ -478,7 +601,7 @@ int coarse_factor(sld_system s, const double* E, double* Einv, double timeout_s,
   }
   if (hst != 0) {
     cudaFreeAsync(A, s->stream);
-    *msg = hst == SLD_ERR_COARSE_SINGULAR ? "E = Z^T A Z is not SPD (Cholesky pivot <= 0)"
+    *msg = hst == SLD_ERR_COARSE_SINGULAR ? "E = Z^T A Z is not SPD (Cholesky pivot <= 0, or below the relative bound)"
                                           : "coarse Cholesky: device wait timed out";
     return hst;
   }
@@ -496,6 +619,35 @@ int coarse_factor(sld_system s, const double* E, double* Einv, double timeout_s,
     return SLD_ERR_CUDA;
   }
   return SLD_OK;
+}
+
+cudaError_t launch_learned_setup(sld_system s, const void* Zextra_dev, int k, int f32, const double* E,
+                                 double* Efull, int* bad) {
+  const int64_t n = s->g.n;
+  const int d = s->d;
+  double* scratch = nullptr;  // ESL (d x kMaxL), ELL (kMaxL x kMaxL), bad flag
+  const size_t nsc = (size_t)d * kMaxL + kMaxL * kMaxL + 2;
+  cudaError_t e = cudaMallocAsync(&scratch, sizeof(double) * nsc, s->stream);
+  if (e != cudaSuccess) return e;
+  double* ESL = scratch;
+  double* ELL = ESL + (size_t)d * kMaxL;
+  int* dbad = reinterpret_cast<int*>(ELL + kMaxL * kMaxL);
+  cudaMemsetAsync(scratch, 0, sizeof(double) * nsc, s->stream);
+  k_learned_pack<<<blocks_for(n, 256), 256, 0, s->stream>>>(n, k, Zextra_dev, f32, s->ZL32, dbad);
+  k_learned_W<<<blocks_for(n, 256), 256, 0, s->stream>>>(s->g, s->Tx, s->Ty, s->Tz, s->diag, s->ZL32, s->WL64,
+                                                         s->WL32);
+  const unsigned grid = (unsigned)std::min<int64_t>(blocks_for(n, 256), (int64_t)s->nsm * 4);
+  k_learned_ESL<<<grid, 256, 0, s->stream>>>(n, s->label, s->WL64, ESL);
+  k_learned_ELL<<<kMaxL * kMaxL, 512, 0, s->stream>>>(n, s->ZL32, s->WL64, ELL);
+  const int D = d + k;
+  k_learned_Efull<<<blocks_for((int64_t)D * D, 256), 256, 0, s->stream>>>(d, k, E, ESL, ELL, Efull);
+  int hbad = 0;
+  cudaMemcpyAsync(&hbad, dbad, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
+  e = cudaStreamSynchronize(s->stream);
+  cudaFreeAsync(scratch, s->stream);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  *bad = hbad;
+  return e;
 }
 
 cudaError_t launch_quantize_fp32(sld_system s) {

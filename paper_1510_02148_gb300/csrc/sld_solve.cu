@@ -53,7 +53,7 @@ struct Sm {
 };
 
 template <typename T, int CX, bool WACC>
-__host__ __device__ constexpr size_t smem_bytes(int d) {
+__host__ __device__ constexpr size_t smem_bytes(int d, int dk) {
   using C = Cfg<T, CX, WACC>;
   size_t b = 0;
   b += sizeof(T) * 2 * (kTY + 2) * C::RS;
@@ -61,15 +61,15 @@ __host__ __device__ constexpr size_t smem_bytes(int d) {
   b += sizeof(T) * 2 * kTY;
   b = (b + 15) / 16 * 16;
   b += sizeof(double) * (size_t)(WACC ? kWarps : 1) * d;
-  b += sizeof(double) * d;
-  b += sizeof(T) * d;
+  b += sizeof(double) * dk;
+  b += sizeof(T) * dk;
   b = (b + 15) / 16 * 16;
   b += sizeof(double) * 64;
   return b;
 }
 
 template <typename T, int CX, bool WACC>
-__device__ Sm<T> carve(unsigned char* base, int d) {
+__device__ Sm<T> carve(unsigned char* base, int d, int dk) {
   using C = Cfg<T, CX, WACC>;
   Sm<T> s;
   size_t o = 0;
@@ -83,9 +83,9 @@ __device__ Sm<T> carve(unsigned char* base, int d) {
   s.acc = reinterpret_cast<double*>(base + o);
   o += sizeof(double) * (size_t)(WACC ? kWarps : 1) * d;
   s.Yd = reinterpret_cast<double*>(base + o);
-  o += sizeof(double) * d;
+  o += sizeof(double) * dk;
   s.Y = reinterpret_cast<T*>(base + o);
-  o += sizeof(T) * d;
+  o += sizeof(T) * dk;
   o = (o + 15) / 16 * 16;
   s.red = reinterpret_cast<double*>(base + o);
   return s;
@@ -374,7 +374,7 @@ __device__ void sweep_A(const SolveArgs& a, const Sm<T>& sm, const T* zb, const 
     }
     part_row[k] = t;
   }
-  if (threadIdx.x == 0) part_row[d + 0] = gsum;
+  if (threadIdx.x == 0) part_row[a.dk + 0] = gsum;
 }
 
 // ---------------------------------------------------------------------------
@@ -608,14 +608,14 @@ __device__ void sweep_B(const SolveArgs& a, const Sm<T>& sm, const T* p, T* zb, 
   const double s1 = block_sum(drho, sm.red);
   const double s2 = block_sum(drr, sm.red);
   if (threadIdx.x == 0) {
-    part_row[a.d + 1] = s1;
-    part_row[a.d + 2] = s2;
+    part_row[a.dk + 1] = s1;
+    part_row[a.dk + 2] = s2;
   }
 }
 
 template <typename T, int CX, bool WACC>
 __device__ __forceinline__ void solve_generic(const SolveArgs& a, unsigned char* smem_raw) {
-  const Sm<T> sm = carve<T, CX, WACC>(smem_raw, a.d);
+  const Sm<T> sm = carve<T, CX, WACC>(smem_raw, a.d, a.dk);
   const T* Fx = static_cast<const T*>(a.Txi);
   const T* Fy = static_cast<const T*>(a.Tyi);
   const T* Fz = static_cast<const T*>(a.Tzi);
@@ -656,7 +656,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve_batch(const SolveArgs* __
 
 template <typename T, int CX, bool WACC>
 int launch(sld_system s, SolveArgs& a, const sld_options& o, float* ms, std::string* msg) {
-  const size_t smem = smem_bytes<T, CX, WACC>(a.d);
+  const size_t smem = smem_bytes<T, CX, WACC>(a.d, a.dk);
   auto kern = k_solve<T, CX, WACC>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) {
@@ -706,6 +706,11 @@ void fill_args(sld_system s, const double* b_dev, const sld_options& o, SolveArg
   a.nty = (s->g.ny + kTY - 1) / kTY;
   a.ntiles = (int64_t)a.ntx * a.nty * s->g.nz;
   a.d = s->d;
+  a.kL = s->kL;
+  a.dk = s->d + s->kL;
+  a.ZL32 = s->ZL32;
+  a.WL64 = s->WL64;
+  a.WLi = fp64 ? (const void*)s->WL64 : (const void*)s->WL32;
   a.label = s->label;
   a.label16 = s->label16;
   // labels from the subdomain-levelset rule with d = S * L keep that structure
@@ -743,7 +748,7 @@ void fill_args(sld_system s, const double* b_dev, const sld_options& o, SolveArg
   a.p1 = s->p1;
   a.xh = s->xh;
   a.part = s->part;
-  a.pstride = (s->d + kPartScalars + 3) / 4 * 4;
+  a.pstride = (a.dk + kPartScalars + 3) / 4 * 4;
   a.s_glob = s->s_glob;
   a.y_glob = s->y_glob;
   a.out = s->out;
@@ -776,6 +781,10 @@ int run_solve(sld_system s, const double* b_dev, const sld_options& o, sld_resul
   const bool use_tma = tma_eligible(s->g) && !(force && std::strcmp(force, "generic") == 0);
   if (bf16 && !use_tma) {
     *msg = "BF16 coefficients are streamed by the TMA sweeps only: they need nx % 8 == 0";
+    return SLD_ERR_INVALID_ARG;
+  }
+  if (s->kL > 0 && (!use_tma || bf16)) {
+    *msg = "extra dense deflation vectors need the TMA sweeps (nx % 8 == 0) and SLD_FP64 or SLD_FP32_IR";
     return SLD_ERR_INVALID_ARG;
   }
   res->kernel_path = use_tma ? 1 : 0;
@@ -878,7 +887,7 @@ int batch_occupancy(size_t smem) {
 
 template <typename T, int CX, bool WACC>
 size_t batch_smem(int dmax) {
-  return smem_bytes<T, CX, WACC>(dmax);
+  return smem_bytes<T, CX, WACC>(dmax, dmax);
 }
 
 }  // namespace

@@ -209,6 +209,7 @@ __device__ void sweep_O1(const SolveArgs& a, double* sacc, double* red, double* 
   for (int k = threadIdx.x; k < (WACC ? kWarps : 1) * d; k += blockDim.x) sacc[k] = 0.0;
   __syncthreads();
   double bb = 0.0;
+  double sl[kMaxL] = {};  // Z_L^T r' (extra columns)
   const int64_t stride = (int64_t)a.sy.ncta * blockDim.x;
   const int64_t nround = (g.n + stride - 1) / stride;
   for (int64_t rnd = 0; rnd < nround; ++rnd) {
@@ -224,8 +225,19 @@ __device__ void sweep_O1(const SolveArgs& a, double* sacc, double* red, double* 
       a.r64[i] = r;
       bb += bi * bi;
       l = a.label[i];
+      if (a.kL > 0) {
+#pragma unroll
+        for (int j = 0; j < kMaxL; ++j) sl[j] += (double)a.ZL32[i * kMaxL + j] * r;
+      }
     }
     warp_flush<WACC>(l, r, sacc, d, warp);
+  }
+#pragma unroll
+  for (int j = 0; j < kMaxL; ++j) {
+    if (j < a.kL) {
+      const double t = block_sum(sl[j], red);
+      if (threadIdx.x == 0) part_row[d + j] = t;
+    }
   }
   const double bsum = block_sum(bb, red);
   for (int k = threadIdx.x; k < d; k += blockDim.x) {
@@ -237,7 +249,7 @@ __device__ void sweep_O1(const SolveArgs& a, double* sacc, double* red, double* 
     }
     part_row[k] = t;
   }
-  if (threadIdx.x == 0) part_row[d + 3] = bsum;
+  if (threadIdx.x == 0) part_row[a.dk + 3] = bsum;
 }
 
 // O2: x += xhat + Z y, rhat = r' - A Z y, z = M^{-1} rhat, xhat = p = 0
@@ -252,9 +264,15 @@ __device__ void sweep_O2(const SolveArgs& a, const double* Yd, double* red, doub
   const int64_t stride = (int64_t)a.sy.ncta * blockDim.x;
   for (int64_t i = (int64_t)team_rank(a.sy) * blockDim.x + threadIdx.x; i < g.n; i += stride) {
     const int ix = (int)(i % g.nx), iy = (int)((i / g.nx) % g.ny), iz = (int)(i / g.nxy);
-    const double AZy = apply64(a, i, ix, iy, iz, [&](int64_t j) { return Yd[__ldg(a.label + j)]; });
+    double AZy = apply64(a, i, ix, iy, iz, [&](int64_t j) { return Yd[__ldg(a.label + j)]; });
+    double Zy = Yd[__ldg(a.label + i)];
+    for (int j = 0; j < a.kL; ++j) {  // extra columns: (A Z_L y_L)_i = (W_L y_L)_i, (Z_L y_L)_i
+      const double yj = Yd[a.d + j];
+      AZy += a.WL64[i * kMaxL + j] * yj;
+      Zy += (double)a.ZL32[i * kMaxL + j] * yj;
+    }
     const double rh = a.r64[i] - AZy;
-    a.x[i] = a.x[i] + (double)xh[i] + Yd[__ldg(a.label + i)];
+    a.x[i] = a.x[i] + (double)xh[i] + Zy;
     const T zt = (T)(rh * (a.invdi ? (double)a.invdi[i] : a.invdiag64[i]));
     zb[i] = zt;
     xh[i] = T(0);
@@ -267,8 +285,8 @@ __device__ void sweep_O2(const SolveArgs& a, const double* Yd, double* red, doub
   const double s1 = block_sum(rho, red);
   const double s2 = block_sum(rr, red);
   if (threadIdx.x == 0) {
-    part_row[a.d + 1] = s1;
-    part_row[a.d + 2] = s2;
+    part_row[a.dk + 1] = s1;
+    part_row[a.dk + 2] = s2;
   }
 }
 
@@ -280,7 +298,7 @@ __device__ void phase_reduce_s(const SolveArgs& a) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nw = blockDim.x >> 5;
   const int G = a.sy.ncta;
-  for (int k = team_rank(a.sy) * nw + warp; k < a.d; k += G * nw) {
+  for (int k = team_rank(a.sy) * nw + warp; k < a.dk; k += G * nw) {
     double t = 0.0;
     for (int c = lane; c < G; c += 32) t += a.part[(int64_t)c * a.pstride + k];
     t = warp_sum(t);
@@ -292,10 +310,10 @@ __device__ void phase_reduce_s(const SolveArgs& a) {
 __device__ void phase_coarse(const SolveArgs& a, const double* Einv) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nw = blockDim.x >> 5;
-  for (int j = team_rank(a.sy) * nw + warp; j < a.d; j += a.sy.ncta * nw) {
-    const double* row = Einv + (int64_t)j * a.d;
+  for (int j = team_rank(a.sy) * nw + warp; j < a.dk; j += a.sy.ncta * nw) {
+    const double* row = Einv + (int64_t)j * a.dk;
     double t = 0.0;
-    for (int k = lane; k < a.d; k += 32) t += __ldg(row + k) * a.s_glob[k];
+    for (int k = lane; k < a.dk; k += 32) t += __ldg(row + k) * a.s_glob[k];
     t = warp_sum(t);
     if (lane == 0) a.y_glob[j] = t;
   }
@@ -306,7 +324,7 @@ __device__ double cta_scalar(const SolveArgs& a, int slot, double* red) {
   __syncthreads();
   if (threadIdx.x < 32) {
     double t = 0.0;
-    for (int c = threadIdx.x; c < a.sy.ncta; c += 32) t += a.part[(int64_t)c * a.pstride + a.d + slot];
+    for (int c = threadIdx.x; c < a.sy.ncta; c += 32) t += a.part[(int64_t)c * a.pstride + a.dk + slot];
     t = warp_sum(t);
     if (threadIdx.x == 0) red[40] = t;
   }
@@ -319,7 +337,7 @@ __device__ double cta_sdoty(const SolveArgs& a, double* red) {
   __syncthreads();
   if (threadIdx.x < 32) {
     double t = 0.0;
-    for (int k = threadIdx.x; k < a.d; k += 32) t += a.s_glob[k] * a.y_glob[k];
+    for (int k = threadIdx.x; k < a.dk; k += 32) t += a.s_glob[k] * a.y_glob[k];
     t = warp_sum(t);
     if (threadIdx.x == 0) red[41] = t;
   }
@@ -356,7 +374,7 @@ __device__ void solve_body(const SolveArgs& a, double* acc, double* Yd, T* Y, do
     phase_coarse(a, a.Einv);
     if (!grid_barrier(a.sy, epoch)) { failed = true; break; }
     if (outer == 0) bb = cta_scalar(a, 3, red);
-    for (int k = threadIdx.x; k < a.d; k += blockDim.x) Yd[k] = a.y_glob[k];
+    for (int k = threadIdx.x; k < a.dk; k += blockDim.x) Yd[k] = a.y_glob[k];
     __syncthreads();
     sweep_O2<T>(a, Yd, red, my_part);
     if (!grid_barrier(a.sy, epoch)) { failed = true; break; }
@@ -390,7 +408,7 @@ __device__ void solve_body(const SolveArgs& a, double* acc, double* Yd, T* Y, do
         break;
       }
       const double alpha = rho / delta;
-      for (int k = threadIdx.x; k < a.d; k += blockDim.x) Y[k] = (T)a.y_glob[k];
+      for (int k = threadIdx.x; k < a.dk; k += blockDim.x) Y[k] = (T)a.y_glob[k];
       __syncthreads();
       if (!sweepB(pold ^ 1, (T)alpha, my_part)) { failed = true; break; }
       if (!grid_barrier(a.sy, epoch)) { failed = true; break; }

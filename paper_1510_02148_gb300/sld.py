@@ -19,6 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsld.so")
 
 OK, ERR_INVALID_ARG, ERR_CUDA, ERR_NOT_CONVERGED, ERR_BREAKDOWN = 0, 1, 2, 3, 4
+ZEXTRA_F64, ZEXTRA_F32 = 0, 1
 ERR_COARSE_SINGULAR, ERR_TIMEOUT, ERR_OOM, ERR_STATE = 5, 6, 7, 8
 STATUS_NAMES = {0: "SLD_OK", 1: "SLD_ERR_INVALID_ARG", 2: "SLD_ERR_CUDA", 3: "SLD_ERR_NOT_CONVERGED",
                 4: "SLD_ERR_BREAKDOWN", 5: "SLD_ERR_COARSE_SINGULAR", 6: "SLD_ERR_TIMEOUT",
@@ -29,7 +30,7 @@ BC_NOFLOW, BC_DIRICHLET = 0, 1
 EXPORTED = ["sld_default_options", "sld_build_system", "sld_make_labels", "sld_build_deflation",
             "sld_solve", "sld_destroy", "sld_last_error", "sld_get_operator", "sld_apply_A",
             "sld_restrict", "sld_get_coarse", "sld_batch_create", "sld_batch_solve",
-            "sld_batch_describe", "sld_batch_destroy", "sld_solve_batched"]
+            "sld_batch_describe", "sld_batch_destroy", "sld_solve_batched", "sld_deflation_info"]
 
 
 class SldError(RuntimeError):
@@ -91,6 +92,7 @@ def load(path: str = LIB_PATH):
         lib.sld_batch_destroy.argtypes = [P]
         lib.sld_batch_destroy.restype = None
         lib.sld_solve_batched.argtypes = [P, C.c_int, P, C.POINTER(Options), P, P]
+        lib.sld_deflation_info.argtypes = [P, P, P, P]
         for name in ("sld_build_system", "sld_make_labels", "sld_build_deflation", "sld_solve",
                      "sld_get_operator", "sld_apply_A", "sld_restrict", "sld_get_coarse",
                      "sld_batch_create", "sld_batch_solve", "sld_solve_batched"):
@@ -193,9 +195,28 @@ class System:
                                       int(L), _ptr(out, np.int32)))
         return out
 
-    def build_deflation(self, d, labels=None):
-        _check(load().sld_build_deflation(self._h, _ptr(labels, np.int32), int(d), None, 0, 0))
+    def build_deflation(self, d, labels=None, Zextra=None):
+        """Z = [label columns, Zextra]: Zextra is n x k (k <= 8), row-major,
+        float64 or float32 (numpy or a torch tensor, host or device)."""
+        k, zp, zdt = 0, None, ZEXTRA_F64
+        if Zextra is not None:
+            if _is_torch(Zextra):
+                import torch
+                zdt = ZEXTRA_F32 if Zextra.dtype == torch.float32 else ZEXTRA_F64
+            else:
+                zdt = ZEXTRA_F32 if Zextra.dtype == np.float32 else ZEXTRA_F64
+            if Zextra.ndim != 2 or Zextra.shape[0] != self.n:
+                raise ValueError("Zextra must be n x k")
+            k = int(Zextra.shape[1])
+            zp = _ptr(Zextra, np.float32 if zdt == ZEXTRA_F32 else np.float64)
+        _check(load().sld_build_deflation(self._h, _ptr(labels, np.int32), int(d), zp, k, zdt))
         self.d = int(d)
+
+    def deflation_info(self):
+        """(d, k_requested, k_used) of the deflation last built."""
+        d, kr, ku = C.c_int(0), C.c_int(0), C.c_int(0)
+        _check(load().sld_deflation_info(self._h, C.byref(d), C.byref(kr), C.byref(ku)))
+        return d.value, kr.value, ku.value
 
     # -- solve ------------------------------------------------------------
     def solve(self, b=None, x=None, options: Optional[Options] = None, raise_on_error=True, **kw):
@@ -229,8 +250,10 @@ class System:
         return out
 
     def get_coarse(self):
-        E = np.empty((self.d, self.d))
-        Einv = np.empty((self.d, self.d))
+        _, _, ku = self.deflation_info()
+        D = self.d + ku
+        E = np.empty((D, D))
+        Einv = np.empty((D, D))
         _check(load().sld_get_coarse(self._h, E.ctypes.data, Einv.ctypes.data))
         return E, Einv
 
