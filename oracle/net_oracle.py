@@ -124,42 +124,54 @@ def unflatten(flat):
     return out
 
 
-def forward(params, f):
+def _ident(a):
+    return a
+
+
+def forward(params, f, rnd=_ident):
     """The U-net: two convolutions at full resolution, three average-pool
     levels (16, 32, 48, 64 channels), nearest-neighbour upsampling with
-    additive skips, and a linear 3x3x3 output convolution to K_OUT channels."""
+    additive skips, and a linear 3x3x3 output convolution to K_OUT channels.
+
+    rnd: applied to every stored activation (the input channels, each conv
+    and pool output except the network output).  The identity gives the FP64
+    network; rounding to BF16 reproduces where a BF16-storage implementation
+    rounds, so that both sides take the same ReLU mask decisions."""
     W = params[0::2]
     B = params[1::2]
-    c = {"f": f}
-    c["a0"] = relu(conv3d(f, W[0], B[0]))
-    c["e0"] = relu(conv3d(c["a0"], W[1], B[1]))
-    c["p1"] = pool(c["e0"])
-    c["e1"] = relu(conv3d(c["p1"], W[2], B[2]))
-    c["p2"] = pool(c["e1"])
-    c["e2"] = relu(conv3d(c["p2"], W[3], B[3]))
-    c["p3"] = pool(c["e2"])
-    c["b3"] = relu(conv3d(c["p3"], W[4], B[4]))
+    c = {"f": rnd(f)}
+    c["a0"] = rnd(relu(conv3d(c["f"], W[0], B[0])))
+    c["e0"] = rnd(relu(conv3d(c["a0"], W[1], B[1])))
+    c["p1"] = rnd(pool(c["e0"]))
+    c["e1"] = rnd(relu(conv3d(c["p1"], W[2], B[2])))
+    c["p2"] = rnd(pool(c["e1"]))
+    c["e2"] = rnd(relu(conv3d(c["p2"], W[3], B[3])))
+    c["p3"] = rnd(pool(c["e2"]))
+    c["b3"] = rnd(relu(conv3d(c["p3"], W[4], B[4])))
     c["u2"] = up(c["b3"])
-    c["d2"] = relu(conv3d(c["u2"], W[5], B[5]) + c["e2"])
+    c["d2"] = rnd(relu(conv3d(c["u2"], W[5], B[5]) + c["e2"]))
     c["u1"] = up(c["d2"])
-    c["d1"] = relu(conv3d(c["u1"], W[6], B[6]) + c["e1"])
+    c["d1"] = rnd(relu(conv3d(c["u1"], W[6], B[6]) + c["e1"]))
     c["u0"] = up(c["d1"])
-    c["d0"] = relu(conv3d(c["u0"], W[7], B[7]) + c["e0"])
+    c["d0"] = rnd(relu(conv3d(c["u0"], W[7], B[7]) + c["e0"]))
     out = conv3d(c["d0"], W[8], B[8])
     return out, c
 
 
-def backward(params, c, dout):
+def backward(params, c, dout, rnd=_ident):
     """Gradients of a scalar with d(scalar)/d(out) = dout, by the chain rule
-    through forward(); returns them in parameter order."""
+    through forward(); returns them in parameter order.  rnd: applied to the
+    masked gradient of each convolution output before it enters that
+    convolution's weight and data gradients (the identity for FP64)."""
     W = params[0::2]
     gW = [None] * 9
     gB = [None] * 9
 
     def conv_back(i, g, x):
-        gW[i] = conv3d_wgrad(g, x)
+        gr = rnd(g)
+        gW[i] = conv3d_wgrad(gr, x)
         gB[i] = g.sum(axis=(0, 1, 2))
-        return conv3d_dgrad(g, W[i])
+        return conv3d_dgrad(gr, W[i])
 
     dd0 = conv_back(8, dout, c["d0"])
     g7 = dd0 * (c["d0"] > 0)

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsld.so")
 SOURCES = ["sld_api.cu", "sld_setup.cu", "sld_solve.cu", "sld_solve_tma.cu", "sld_solve_tma_learned.cu",
-           "sld_noalloc.cu"]
+           "sld_noalloc.cu", "sld_net.cu", "sld_lanczos.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xptxas", "-warn-spills"]
@@ -34,7 +34,8 @@ def _stale() -> bool:
         return True
     t = os.path.getmtime(LIB)
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
-    deps.append(os.path.join(HERE, "..", "include", "sld.h"))
+    inc_dir = os.path.join(HERE, "..", "include")
+    deps += [os.path.join(inc_dir, f) for f in os.listdir(inc_dir)]
     return any(os.path.getmtime(p) > t for p in deps if os.path.exists(p))
 
 

@@ -30,7 +30,10 @@ BC_NOFLOW, BC_DIRICHLET = 0, 1
 EXPORTED = ["sld_default_options", "sld_build_system", "sld_make_labels", "sld_build_deflation",
             "sld_solve", "sld_destroy", "sld_last_error", "sld_get_operator", "sld_apply_A",
             "sld_restrict", "sld_get_coarse", "sld_batch_create", "sld_batch_solve",
-            "sld_batch_describe", "sld_batch_destroy", "sld_solve_batched", "sld_deflation_info"]
+            "sld_batch_describe", "sld_batch_destroy", "sld_solve_batched", "sld_deflation_info",
+            "sld_net_num_params", "sld_net_create", "sld_net_set_params", "sld_net_get_params",
+            "sld_net_get_grads", "sld_net_forward", "sld_net_backward", "sld_net_loss_backward",
+            "sld_net_adam", "sld_net_destroy", "sld_lanczos_eigvecs"]
 
 
 class SldError(RuntimeError):
@@ -93,6 +96,19 @@ def load(path: str = LIB_PATH):
         lib.sld_batch_destroy.restype = None
         lib.sld_solve_batched.argtypes = [P, C.c_int, P, C.POINTER(Options), P, P]
         lib.sld_deflation_info.argtypes = [P, P, P, P]
+        lib.sld_net_num_params.argtypes = []
+        lib.sld_net_num_params.restype = C.c_int64
+        lib.sld_net_create.argtypes = [C.c_int, C.c_int, C.c_int, P, C.POINTER(P)]
+        lib.sld_net_set_params.argtypes = [P, P]
+        lib.sld_net_get_params.argtypes = [P, P]
+        lib.sld_net_get_grads.argtypes = [P, P]
+        lib.sld_net_forward.argtypes = [P, P, P]
+        lib.sld_net_backward.argtypes = [P, P]
+        lib.sld_net_loss_backward.argtypes = [P, P, C.c_int, P, C.POINTER(C.c_double)]
+        lib.sld_net_adam.argtypes = [P, C.c_float, C.c_float, C.c_float, C.c_float, C.c_int]
+        lib.sld_net_destroy.argtypes = [P]
+        lib.sld_net_destroy.restype = None
+        lib.sld_lanczos_eigvecs.argtypes = [P, C.c_int, C.c_int, P, P, P]
         for name in ("sld_build_system", "sld_make_labels", "sld_build_deflation", "sld_solve",
                      "sld_get_operator", "sld_apply_A", "sld_restrict", "sld_get_coarse",
                      "sld_batch_create", "sld_batch_solve", "sld_solve_batched"):
@@ -314,3 +330,85 @@ class Batch:
         except Exception:
             pass
 
+
+
+# ---------------------------------------------------------------------------
+# Deflation-vector network and the Lanczos targets (include/sld_net.h)
+# ---------------------------------------------------------------------------
+NET_K = 8
+
+
+def net_num_params() -> int:
+    return int(load().sld_net_num_params())
+
+
+class Net:
+    """The deflation-vector U-net for nx x ny x nz grids (multiples of 8).
+    Arrays may be numpy (host) or torch tensors (device)."""
+
+    def __init__(self, shape, stream=None):
+        nz, ny, nx = shape
+        h = C.c_void_p()
+        _check(load().sld_net_create(int(nx), int(ny), int(nz), stream, C.byref(h)))
+        self._h = h
+        self.shape = (nz, ny, nx)
+        self.n = nx * ny * nz
+        self.np = net_num_params()
+
+    def set_params(self, p):
+        _check(load().sld_net_set_params(self._h, _ptr(p, np.float32)))
+
+    def get_params(self, out=None):
+        out = np.empty(self.np, dtype=np.float32) if out is None else out
+        _check(load().sld_net_get_params(self._h, _ptr(out, np.float32)))
+        return out
+
+    def get_grads(self, out=None):
+        out = np.empty(self.np, dtype=np.float32) if out is None else out
+        _check(load().sld_net_get_grads(self._h, _ptr(out, np.float32)))
+        return out
+
+    def forward(self, K, out=None, keep=False):
+        """n x 8 FP32 vectors for permeability K (n FP64 values)."""
+        if keep:
+            _check(load().sld_net_forward(self._h, _ptr(K, np.float64), None))
+            return None
+        out = np.empty((self.n, NET_K), dtype=np.float32) if out is None else out
+        _check(load().sld_net_forward(self._h, _ptr(K, np.float64), _ptr(out, np.float32)))
+        return out
+
+    def backward(self, dout):
+        _check(load().sld_net_backward(self._h, _ptr(dout, np.float32)))
+
+    def loss_backward(self, V, D):
+        """Subspace loss of the last forward output against V (n x m FP32)
+        with weights D (n FP64); fills the parameter gradients."""
+        loss = C.c_double(0.0)
+        _check(load().sld_net_loss_backward(self._h, _ptr(V, np.float32), int(V.shape[1]), _ptr(D, np.float64),
+                                            C.byref(loss)))
+        return loss.value
+
+    def adam(self, lr, step, beta1=0.9, beta2=0.999, eps=1e-8):
+        _check(load().sld_net_adam(self._h, float(lr), float(beta1), float(beta2), float(eps), int(step)))
+
+    def close(self):
+        if self._h:
+            load().sld_net_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def lanczos_eigvecs(system: System, k=8, m=40, vecs=None):
+    """k smallest nonzero eigenpairs of M^{-1} P A (label deflation) by m
+    shift-invert Lanczos steps: (values, n x k FP32 vectors, residuals)."""
+    vals = np.empty(k)
+    res = np.empty(k)
+    vecs = np.empty((system.n, k), dtype=np.float32) if vecs is None else vecs
+    _check(load().sld_lanczos_eigvecs(system._h, int(k), int(m), vals.ctypes.data, _ptr(vecs, np.float32),
+                                      res.ctypes.data))
+    return vals, vecs, res

@@ -1,5 +1,5 @@
-"""The C-ABI library builds, loads and exports every entry point that
-include/sld.h declares (no compute calls: this runs without a GPU)."""
+"""The C-ABI library builds, loads and exports every entry point that the
+headers under include/ declare (no compute calls: this runs without a GPU)."""
 import ctypes
 import os
 import re
@@ -10,7 +10,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _declared():
-    src = open(os.path.join(ROOT, "include", "sld.h")).read()
+    inc = os.path.join(ROOT, "include")
+    src = "".join(open(os.path.join(inc, f)).read() for f in sorted(os.listdir(inc)) if f.endswith(".h"))
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"\b(sld_[A-Za-z_0-9]+)\s*\(", src)))
 
@@ -27,7 +28,8 @@ def libpath():
 def test_header_declares_entry_points():
     names = _declared()
     for must in ("sld_build_system", "sld_make_labels", "sld_build_deflation", "sld_solve",
-                 "sld_destroy", "sld_last_error"):
+                 "sld_destroy", "sld_last_error", "sld_net_forward", "sld_net_loss_backward",
+                 "sld_lanczos_eigvecs"):
         assert must in names
 
 
