@@ -178,6 +178,57 @@ def bench_batched(sld, torch, reps=3):
     return out
 
 
+LEARNED_WEIGHTS = os.path.join(ROOT, "paper_1510_02148_gb300", "data", "learned_c4.npz")
+
+
+def bench_learned(sld, torch, nfields=4):
+    """Learned extra deflation vectors on held-out 128^3 lognormal-layered
+    fields (contrast 10^c, c ~ U[4, 6], 4x4x2 subdomains x 2 levelsets = 64
+    label columns + 8 learned): FP32-inner solves with label deflation alone
+    vs label + learned columns, and plain FP64 label deflation; the network
+    weights are the committed ones trained by paper_1510_02148_gb300.learned."""
+    from paper_1510_02148_gb300 import learned
+    if not os.path.exists(LEARNED_WEIGHTS):
+        return {"unavailable": "no trained weights committed"}
+    params, meta = learned.load_params(LEARNED_WEIGHTS)
+    n = int(meta["n"])
+    net = sld.Net((n, n, n))
+    net.set_params(params.astype(np.float32))
+    rows = []
+    for seed in range(learned.EVAL_SEED0, learned.EVAL_SEED0 + nfields):
+        P = learned.field(seed, n)
+        s = learned.build_system(P)
+        x = torch.empty(P.n, dtype=torch.float64, device="cuda")
+        s.solve(x=x, precision=sld.FP64)
+        _, f64 = s.solve(x=x, precision=sld.FP64)
+        s.solve(x=x, precision=sld.FP32_IR)
+        _, f32 = s.solve(x=x, precision=sld.FP32_IR)
+        Y = torch.empty((P.n, 8), dtype=torch.float32, device="cuda")
+        t0 = time.perf_counter()
+        net.forward(torch.from_numpy(P.K.reshape(-1)).cuda(), out=Y)
+        s.build_deflation(P.d, Zextra=Y)
+        torch.cuda.synchronize()
+        setup_ms = (time.perf_counter() - t0) * 1e3
+        ku = s.deflation_info()[2]
+        s.solve(x=x, precision=sld.FP32_IR)
+        _, lrn = s.solve(x=x, precision=sld.FP32_IR)
+        rows.append((f64, f32, lrn, setup_ms, ku))
+        s.close()
+    net.close()
+    med = lambda v: float(statistics.median(v))  # noqa: E731
+    return {"workload": f"held-out learned-case fields {n}^3 (seeds {learned.EVAL_SEED0}..), d = 64 + 8 learned",
+            "fields": nfields, "trained_on": meta,
+            "fp64_plain_ms": med([r[0].solve_ms for r in rows]), "fp64_plain_its": med([r[0].iterations for r in rows]),
+            "fp32ir_plain_ms": med([r[1].solve_ms for r in rows]),
+            "fp32ir_plain_its": med([r[1].iterations for r in rows]),
+            "fp32ir_learned_ms": med([r[2].solve_ms for r in rows]),
+            "fp32ir_learned_its": med([r[2].iterations for r in rows]),
+            "learned_setup_ms": med([r[3] for r in rows]), "k_used": [r[4] for r in rows],
+            "max_true_relres": max(r[2].true_relres for r in rows),
+            "speedup_learned_vs_fp64_plain": med([r[0].solve_ms / r[2].solve_ms for r in rows]),
+            "speedup_learned_vs_fp32ir_plain": med([r[1].solve_ms / r[2].solve_ms for r in rows])}
+
+
 def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
@@ -240,6 +291,7 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--profile-solve", choices=["fp64", "fp32_ir", "bf16"], default=None,
                     help="set up the workload and run one solve (for profiler captures); no timing line")
@@ -355,6 +407,8 @@ def main():
     }
     if not args.no_batched:
         line["batched"] = bench_batched(sld, torch)
+    if not args.no_learned:
+        line["learned"] = bench_learned(sld, torch)
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(P, iters_full=fp64[-1].iterations, sample_iters=30)
     s.close()
