@@ -93,16 +93,25 @@ struct LabelAcc {
     }
     run = T(0);
   }
+  // The group sums are formed in the inner precision T (FP32 in the mixed
+  // solve: the run sums already are), in a fixed order: a 5-step butterfly
+  // when the whole warp is one group (the usual case), else lane order.
   __device__ __forceinline__ void flush_group(int key, int nk, double* sacc, int d, int warp) {
     const int lane = threadIdx.x & 31;
     const unsigned grp = __match_any_sync(kFull, key);
     for (int k = 0; k < nk; ++k) {
-      const double mine = (double)(L == 0 ? run : (k == 0 ? a0 : k == 1 ? a1 : k == 2 ? a2 : a3));
-      double sum = 0.0;
+      const T mine = L == 0 ? run : (k == 0 ? a0 : k == 1 ? a1 : k == 2 ? a2 : a3);
+      T sum = T(0);
+      if (grp == kFull) {
+        sum = mine;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(kFull, sum, o);
+      } else {
 #pragma unroll 4
-      for (int src = 0; src < 32; ++src) {
-        const double v = __shfl_sync(kFull, mine, src);
-        if ((grp >> src) & 1u) sum += v;
+        for (int src = 0; src < 32; ++src) {
+          const T v = __shfl_sync(kFull, mine, src);
+          if ((grp >> src) & 1u) sum += v;
+        }
       }
       if (key >= 0 && lane == __ffs(grp) - 1) {
         const int slot = L > 0 ? key * L + k : key;

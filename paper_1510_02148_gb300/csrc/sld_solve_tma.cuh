@@ -87,23 +87,28 @@ struct Maps {
 };
 
 // The CTA's sequence of planes to load: for every segment (column tile ct,
-// planes z0 .. z1-1) the planes z0-1 .. z1 (the z neighbours included).
+// planes z0 .. z1-1) the planes z0-1 .. z1 (the z neighbours included); the
+// tile origin (x0, y0) is computed once per segment.
 struct Walk {
-  int64_t t, t1, ct;
-  int nz, z0, z1, k, kn;
-  __device__ void begin(int64_t a, int64_t b, int nz_) {
+  int64_t t, t1;
+  int nz, ntx, ty, z0, z1, k, kn, x0, y0;
+  __device__ void begin(int64_t a, int64_t b, int nz_, int ntx_, int ty_) {
     t = a;
     t1 = b;
     nz = nz_;
+    ntx = ntx_;
+    ty = ty_;
     load();
   }
   __device__ void load() {
     if (t < t1) {
-      ct = t / nz;
+      const int64_t ct = t / nz;
       z0 = (int)(t % nz);
       z1 = (int)((int64_t)nz < z0 + (t1 - t) ? (int64_t)nz : z0 + (t1 - t));
       k = 0;
       kn = z1 - z0 + 2;
+      x0 = (int)(ct % ntx) * kTX;
+      y0 = (int)(ct / ntx) * ty;
     }
   }
   __device__ bool more() const { return t < t1; }
@@ -172,13 +177,15 @@ __device__ void ring_drain(const Ring<S>& rg, const SyncArgs& sy, uint64_t from,
   __syncthreads();
 }
 
+// Loads of one plane item into its ring slot (one thread): arm the slot's
+// mbarrier with the plane's byte count, then issue every box.
 template <typename T, typename F, int TY, int S, bool IS_A>
-__device__ __forceinline__ void issue(const Ring<S>& rg, const Maps& mp, const SolveArgs& a, int ntx, uint64_t item,
-                                      int64_t ct, int pz, int pbuf) {
+__device__ __forceinline__ void issue(const Ring<S>& rg, const Maps& mp, uint64_t item, int x0, int y0, int pz,
+                                      int pbuf) {
   using C = TCfg<T, F, TY>;
-  unsigned char* st = rg.slot(item);
-  uint64_t* bar = rg.full + (item % S);
-  const int x0 = (int)(ct % ntx) * kTX, y0 = (int)(ct / ntx) * TY;
+  const unsigned si = (unsigned)(item % S);
+  unsigned char* st = rg.slots + (size_t)si * rg.slot_bytes;
+  uint64_t* bar = rg.full + si;
   if constexpr (IS_A) {
     mbar_expect_tx(bar, C::TX_A);
     tma_load_3d(st + C::A_ZB, &mp.zb_h, bar, x0 - C::H, y0 - 1, pz);
@@ -247,17 +254,22 @@ __device__ bool sweep_tma(const SolveArgs& a, const Maps& mp, const Ring<S>& rg,
   uint64_t released = gitem;  // items below this are free
   uint64_t issued = gitem;    // thread 0 only
   Walk pw;
+  // Global data read by this sweep's TMA loads was written before the last
+  // grid barrier (each sweep and refinement step ends with a proxy fence
+  // before it); one fence here orders this thread's own earlier writes.  No
+  // fence per refill: it would wait for the thread's in-flight stores of the
+  // plane just computed, which no TMA load of this sweep reads.
+  if (tid == 0) fence_proxy_async();
   auto refill = [&]() {
     if (tid == 0) {
-      fence_proxy_async();
       while (pw.more() && issued < released + S) {
-        issue<T, F, TY, S, IS_A>(rg, mp, a, ntx, issued, pw.ct, pw.plane(), pbuf);
+        issue<T, F, TY, S, IS_A>(rg, mp, issued, pw.x0, pw.y0, pw.plane(), pbuf);
         ++issued;
         pw.next();
       }
     }
   };
-  if (tid == 0) pw.begin(t0, t1, g.nz);
+  if (tid == 0) pw.begin(t0, t1, g.nz, ntx, TY);
   __syncthreads();
   refill();
   uint64_t item = gitem;
@@ -597,6 +609,8 @@ __global__ void __launch_bounds__(16 * TY) k_solve_tma(SolveArgs a, const __grid
     for (int k = 0; k < S; ++k) mbar_init(rg.full + k, 1);
     fence_mbar_init();
   }
+  if (threadIdx.x < (int)(sizeof(Maps) / sizeof(CUtensorMap)))  // descriptors into the TMA unit's cache
+    prefetch_tensormap(reinterpret_cast<const CUtensorMap*>(&mp) + threadIdx.x);
   __syncthreads();
   T* pb[2] = {static_cast<T*>(a.p0), static_cast<T*>(a.p1)};
   uint64_t gitem = 0;
