@@ -96,8 +96,10 @@ sld_status ensure_workspace(sld_system s, bool need_fp32, bool need_bf16) {
     s->part_rows = s->nsm * 8;
     const int pstride = (sld::kMaxD + sld::kMaxL + sld::kPartScalars + 3) / 4 * 4;
     if ((e = dalloc(&s->part, (size_t)s->part_rows * pstride)) != cudaSuccess) return cuda_fail(e, "alloc partials");
-    if ((e = dalloc(&s->s_glob, sld::kMaxD + sld::kMaxL)) != cudaSuccess) return cuda_fail(e, "alloc s");
-    if ((e = dalloc(&s->y_glob, sld::kMaxD + sld::kMaxL)) != cudaSuccess) return cuda_fail(e, "alloc y");
+    if ((e = dalloc(&s->s_glob, sld::kMaxD + sld::kMaxL + sld::kPartScalars)) != cudaSuccess)
+      return cuda_fail(e, "alloc s");
+    if ((e = dalloc(&s->y_glob, sld::kMaxD + sld::kMaxL + sld::kPartScalars)) != cudaSuccess)
+      return cuda_fail(e, "alloc y");
   }
   if (need_fp32 && !s->Tx32) {
     if ((e = dalloc(&s->Tx32, n)) != cudaSuccess) return cuda_fail(e, "alloc Tx32");

@@ -372,9 +372,9 @@ __device__ void sweep_A(const SolveArgs& a, const Sm<T>& sm, const T* zb, const 
     } else {
       t = sm.acc[k];
     }
-    part_row[k] = t;
+    part_row[(int64_t)(k) * a.pstride] = t;
   }
-  if (threadIdx.x == 0) part_row[a.dk + 0] = gsum;
+  if (threadIdx.x == 0) part_row[(int64_t)(a.dk + 0) * a.pstride] = gsum;
 }
 
 // ---------------------------------------------------------------------------
@@ -608,8 +608,8 @@ __device__ void sweep_B(const SolveArgs& a, const Sm<T>& sm, const T* p, T* zb, 
   const double s1 = block_sum(drho, sm.red);
   const double s2 = block_sum(drr, sm.red);
   if (threadIdx.x == 0) {
-    part_row[a.dk + 1] = s1;
-    part_row[a.dk + 2] = s2;
+    part_row[(int64_t)(a.dk + 1) * a.pstride] = s1;
+    part_row[(int64_t)(a.dk + 2) * a.pstride] = s2;
   }
 }
 
@@ -748,7 +748,7 @@ void fill_args(sld_system s, const double* b_dev, const sld_options& o, SolveArg
   a.p1 = s->p1;
   a.xh = s->xh;
   a.part = s->part;
-  a.pstride = (a.dk + kPartScalars + 3) / 4 * 4;
+  a.pstride = s->part_rows;  // column-major partials: one slot per CTA
   a.s_glob = s->s_glob;
   a.y_glob = s->y_glob;
   a.out = s->out;

@@ -245,7 +245,7 @@ __device__ void sweep_O1(const SolveArgs& a, double* sacc, double* red, double* 
   for (int j = 0; j < kMaxL; ++j) {
     if (j < a.kL) {
       const double t = block_sum(sl[j], red);
-      if (threadIdx.x == 0) part_row[d + j] = t;
+      if (threadIdx.x == 0) part_row[(int64_t)(d + j) * a.pstride] = t;
     }
   }
   const double bsum = block_sum(bb, red);
@@ -256,9 +256,9 @@ __device__ void sweep_O1(const SolveArgs& a, double* sacc, double* red, double* 
     } else {
       t = sacc[k];
     }
-    part_row[k] = t;
+    part_row[(int64_t)(k) * a.pstride] = t;
   }
-  if (threadIdx.x == 0) part_row[a.dk + 3] = bsum;
+  if (threadIdx.x == 0) part_row[(int64_t)(a.dk + 3) * a.pstride] = bsum;
 }
 
 // O2: x += xhat + Z y, rhat = r' - A Z y, z = M^{-1} rhat, xhat = p = 0
@@ -294,22 +294,27 @@ __device__ void sweep_O2(const SolveArgs& a, const double* Yd, double* red, doub
   const double s1 = block_sum(rho, red);
   const double s2 = block_sum(rr, red);
   if (threadIdx.x == 0) {
-    part_row[a.dk + 1] = s1;
-    part_row[a.dk + 2] = s2;
+    part_row[(int64_t)(a.dk + 1) * a.pstride] = s1;
+    part_row[(int64_t)(a.dk + 2) * a.pstride] = s2;
   }
 }
 
 // ---------------------------------------------------------------------------
 // Grid-wide phases on the partial sums.
 // ---------------------------------------------------------------------------
-// s_k = sum over CTAs of part[c][k], one warp per column, fixed order.
-__device__ void phase_reduce_s(const SolveArgs& a) {
+// Partial sums are stored column-major: part[k * pstride + c] is CTA c's
+// contribution to column k (coarse sums k < dk, then the scalar slots), so a
+// column is one contiguous run.
+// s_k = sum over CTAs of column k, one warp per column, fixed order; columns
+// k < dk + extra (extra = 1: the scalar slot dk + 0 as well, into s_glob[dk]).
+__device__ void phase_reduce_s(const SolveArgs& a, int extra = 0) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nw = blockDim.x >> 5;
   const int G = a.sy.ncta;
-  for (int k = team_rank(a.sy) * nw + warp; k < a.dk; k += G * nw) {
+  for (int k = team_rank(a.sy) * nw + warp; k < a.dk + extra; k += G * nw) {
+    const double* col = a.part + (int64_t)k * a.pstride;
     double t = 0.0;
-    for (int c = lane; c < G; c += 32) t += a.part[(int64_t)c * a.pstride + k];
+    for (int c = lane; c < G; c += 32) t += col[c];
     t = warp_sum(t);
     if (lane == 0) a.s_glob[k] = t;
   }
@@ -328,17 +333,27 @@ __device__ void phase_coarse(const SolveArgs& a, const double* Einv) {
   }
 }
 
-// Sum of one scalar slot over all CTAs (same order in every CTA).
-__device__ double cta_scalar(const SolveArgs& a, int slot, double* red) {
+// Sums of two scalar slots over all CTAs (same order in every CTA), by
+// warps 0 and 1 at once.
+__device__ void cta_scalar2(const SolveArgs& a, int slot0, int slot1, double* red, double* v0, double* v1) {
   __syncthreads();
-  if (threadIdx.x < 32) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp < 2) {
+    const double* col = a.part + (int64_t)(a.dk + (warp ? slot1 : slot0)) * a.pstride;
     double t = 0.0;
-    for (int c = threadIdx.x; c < a.sy.ncta; c += 32) t += a.part[(int64_t)c * a.pstride + a.dk + slot];
+    for (int c = lane; c < a.sy.ncta; c += 32) t += col[c];
     t = warp_sum(t);
-    if (threadIdx.x == 0) red[40] = t;
+    if (lane == 0) red[40 + warp] = t;
   }
   __syncthreads();
-  return red[40];
+  *v0 = red[40];
+  *v1 = red[41];
+}
+
+__device__ double cta_scalar(const SolveArgs& a, int slot, double* red) {
+  double v0, v1;
+  cta_scalar2(a, slot, slot, red, &v0, &v1);
+  return v0;
 }
 
 // s . y (same order in every CTA).
@@ -348,10 +363,10 @@ __device__ double cta_sdoty(const SolveArgs& a, double* red) {
     double t = 0.0;
     for (int k = threadIdx.x; k < a.dk; k += 32) t += a.s_glob[k] * a.y_glob[k];
     t = warp_sum(t);
-    if (threadIdx.x == 0) red[41] = t;
+    if (threadIdx.x == 0) red[42] = t;
   }
   __syncthreads();
-  return red[41];
+  return red[42];
 }
 
 
@@ -367,7 +382,7 @@ __device__ double cta_sdoty(const SolveArgs& a, double* red) {
 template <typename T, bool WACC, class SweepA, class SweepB>
 __device__ void solve_body(const SolveArgs& a, double* acc, double* Yd, T* Y, double* red, SweepA&& sweepA,
                            SweepB&& sweepB) {
-  double* my_part = a.part + (int64_t)team_rank(a.sy) * a.pstride;
+  double* my_part = a.part + team_rank(a.sy);  // column-major: stride a.pstride
   unsigned epoch = 0;
   const double tol2 = a.tol * a.tol;
   double bb = 0.0, rr_outer = 0.0, rho = 0.0, rec_rr = 0.0;
@@ -387,8 +402,7 @@ __device__ void solve_body(const SolveArgs& a, double* acc, double* Yd, T* Y, do
     __syncthreads();
     sweep_O2<T>(a, Yd, red, my_part);
     if (!grid_barrier(a.sy, epoch)) { failed = true; break; }
-    rho = cta_scalar(a, 1, red);
-    rr_outer = cta_scalar(a, 2, red);
+    cta_scalar2(a, 1, 2, red, &rho, &rr_outer);
     ++outer;
     if (!isfinite(rr_outer) || !isfinite(rho)) { status = SLD_ERR_BREAKDOWN; break; }
     if (a.fp64) {
@@ -406,11 +420,11 @@ __device__ void solve_body(const SolveArgs& a, double* acc, double* Yd, T* Y, do
     for (;;) {
       if (!sweepA(pold, (T)beta, my_part)) { failed = true; break; }
       if (!grid_barrier(a.sy, epoch)) { failed = true; break; }
-      phase_reduce_s(a);
+      phase_reduce_s(a, 1);  // and gamma into s_glob[dk]
       if (!grid_barrier(a.sy, epoch)) { failed = true; break; }
       phase_coarse(a, a.Einv_inner);
       if (!grid_barrier(a.sy, epoch)) { failed = true; break; }
-      const double gamma = cta_scalar(a, 0, red);
+      const double gamma = a.s_glob[a.dk];
       const double delta = gamma - cta_sdoty(a, red);
       if (!(delta > 0.0) || !isfinite(delta) || !isfinite(rho)) {
         if (a.fp64) status = SLD_ERR_BREAKDOWN;
@@ -421,8 +435,8 @@ __device__ void solve_body(const SolveArgs& a, double* acc, double* Yd, T* Y, do
       __syncthreads();
       if (!sweepB(pold ^ 1, (T)alpha, my_part)) { failed = true; break; }
       if (!grid_barrier(a.sy, epoch)) { failed = true; break; }
-      const double rho_new = cta_scalar(a, 1, red);
-      const double rr = cta_scalar(a, 2, red);
+      double rho_new, rr;
+      cta_scalar2(a, 1, 2, red, &rho_new, &rr);
       ++its;
       if (a.fp64) rec_rr = rr;
       if (rr <= tgt2) {

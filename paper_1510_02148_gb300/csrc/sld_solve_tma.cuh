@@ -547,23 +547,23 @@ __device__ bool sweep_tma(const SolveArgs& a, const Maps& mp, const Ring<S>& rg,
       } else {
         s = sacc[k];
       }
-      part_row[k] = s;
+      part_row[(int64_t)(k) * a.pstride] = s;
     }
-    if (tid == 0) part_row[a.dk + 0] = gsum;
+    if (tid == 0) part_row[(int64_t)(a.dk + 0) * a.pstride] = gsum;
     if constexpr (LRN) {
       // block_sum above ended with a CTA barrier: every lsum row is final
       for (int j = tid; j < a.kL; j += blockDim.x) {
         double t = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += lsum[w * kMaxL + j];
-        part_row[d + j] = t;
+        part_row[(int64_t)(d + j) * a.pstride] = t;
       }
     }
   } else {
     const double s1 = block_sum(dacc1, red);
     const double s2 = block_sum(dacc2, red);
     if (tid == 0) {
-      part_row[a.dk + 1] = s1;
-      part_row[a.dk + 2] = s2;
+      part_row[(int64_t)(a.dk + 1) * a.pstride] = s1;
+      part_row[(int64_t)(a.dk + 2) * a.pstride] = s2;
     }
   }
   return true;
