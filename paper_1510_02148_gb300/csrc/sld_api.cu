@@ -81,9 +81,12 @@ sld_status ensure_workspace(sld_system s, bool need_fp32, bool need_bf16) {
     if ((e = dalloc(&s->x, n)) != cudaSuccess) return cuda_fail(e, "alloc x");
     if ((e = dalloc(&s->r64, n)) != cudaSuccess) return cuda_fail(e, "alloc r");
     if ((e = dalloc(&s->bwork, n)) != cudaSuccess) return cuda_fail(e, "alloc b");
+    // inner vectors: n FP64 (FP64 form, rows unpadded) or np FP32 (padded rows)
+    const int64_t nv = std::max<int64_t>(n, (s->np + 1) / 2);
+    s->nvec = nv;
     double* v[4];
     for (int k = 0; k < 4; ++k)
-      if ((e = dalloc(&v[k], n)) != cudaSuccess) return cuda_fail(e, "alloc vectors");
+      if ((e = dalloc(&v[k], nv)) != cudaSuccess) return cuda_fail(e, "alloc vectors");
     s->z = v[0];
     s->p0 = v[1];
     s->p1 = v[2];
@@ -102,9 +105,9 @@ sld_status ensure_workspace(sld_system s, bool need_fp32, bool need_bf16) {
       return cuda_fail(e, "alloc y");
   }
   if (need_fp32 && !s->Tx32) {
-    if ((e = dalloc(&s->Tx32, n)) != cudaSuccess) return cuda_fail(e, "alloc Tx32");
-    if ((e = dalloc(&s->Ty32, n)) != cudaSuccess) return cuda_fail(e, "alloc Ty32");
-    if ((e = dalloc(&s->Tz32, n)) != cudaSuccess) return cuda_fail(e, "alloc Tz32");
+    if ((e = dalloc(&s->Tx32, s->np)) != cudaSuccess) return cuda_fail(e, "alloc Tx32");
+    if ((e = dalloc(&s->Ty32, s->np)) != cudaSuccess) return cuda_fail(e, "alloc Ty32");
+    if ((e = dalloc(&s->Tz32, s->np)) != cudaSuccess) return cuda_fail(e, "alloc Tz32");
     if ((e = sld::launch_quantize_fp32(s)) != cudaSuccess) return cuda_fail(e, "fp32 coefficients");
   }
   if (need_bf16 && !s->bf16_ready) {
@@ -112,10 +115,10 @@ sld_status ensure_workspace(sld_system s, bool need_fp32, bool need_bf16) {
     // quantized operator with its inverse (the inner iterations deflate with
     // the operator they apply)
     if (!s->Tx16) {
-      if ((e = dalloc(&s->Tx16, n)) != cudaSuccess) return cuda_fail(e, "alloc Tx16");
-      if ((e = dalloc(&s->Ty16, n)) != cudaSuccess) return cuda_fail(e, "alloc Ty16");
-      if ((e = dalloc(&s->Tz16, n)) != cudaSuccess) return cuda_fail(e, "alloc Tz16");
-      if ((e = dalloc(&s->invd16, n)) != cudaSuccess) return cuda_fail(e, "alloc invd16");
+      if ((e = dalloc(&s->Tx16, s->np)) != cudaSuccess) return cuda_fail(e, "alloc Tx16");
+      if ((e = dalloc(&s->Ty16, s->np)) != cudaSuccess) return cuda_fail(e, "alloc Ty16");
+      if ((e = dalloc(&s->Tz16, s->np)) != cudaSuccess) return cuda_fail(e, "alloc Tz16");
+      if ((e = dalloc(&s->invd16, s->np)) != cudaSuccess) return cuda_fail(e, "alloc invd16");
     }
     dfree(s->E16);
     dfree(s->Einv16);
@@ -197,6 +200,8 @@ sld_status sld_build_system(const double* K, const double* q, sld_grid g, sld_bc
   s->g.nz = g.nz;
   s->g.nxy = (int64_t)g.nx * g.ny;
   s->g.n = n;
+  s->nxp = (g.nx + 7) / 8 * 8;
+  s->np = (int64_t)s->nxp * g.ny * g.nz;
   for (int f = 0; f < 6; ++f) {
     s->bc_type[f] = bc.type[f];
     s->bc_value[f] = bc.value[f];
@@ -321,7 +326,7 @@ sld_status sld_build_deflation(sld_system s, const int32_t* labels, int d, const
   if ((e = sld::launch_coarse_E(s, s->Tx, s->Ty, s->Tz, s->E, &bad)) != cudaSuccess)
     return cuda_fail(e, "coarse matrix");
   if (bad) return fail(SLD_ERR_INVALID_ARG, "a label is outside [0, d)");
-  if (!s->label16 && (e = dalloc(&s->label16, s->g.n)) != cudaSuccess) return cuda_fail(e, "alloc labels16");
+  if (!s->label16 && (e = dalloc(&s->label16, s->np)) != cudaSuccess) return cuda_fail(e, "alloc labels16");
   if ((e = sld::launch_labels16(s)) != cudaSuccess) return cuda_fail(e, "labels16");
   std::string msg;
   if (k > 0) {
@@ -612,6 +617,7 @@ sld_status sld_batch_create(sld_system* systems, int count, const sld_options* o
   // candidate launch shapes: CTAs per SM, team-size exponent, cells per lane
   bool all4 = true;
   for (int k = 0; k < count; ++k) all4 = all4 && systems[k]->g.nx % 4 == 0 && systems[k]->g.nx >= 96;
+  if (o.precision != SLD_FP64) all4 = false;  // the FP32-inner batch runs on the TMA sweeps (no cx choice)
   struct Cand { int per; double expo; int cx; };
   std::vector<Cand> cands;
   for (int cx : (all4 ? std::vector<int>{1, 4} : std::vector<int>{1}))
@@ -695,8 +701,9 @@ sld_status sld_batch_create(sld_system* systems, int count, const sld_options* o
   }
   const sld::BatchPlan& p = bt->plan;
   bt->desc = "systems " + std::to_string(count) + ", CTAs " + std::to_string(p.G) + " (" + std::to_string(p.per_sm) +
-             " per SM), cells per lane " + std::to_string(p.cx) + ", teams by " +
-             (p.expo < 0 ? std::string("measured work") : "n^" + std::to_string(p.expo).substr(0, 4)) + ":";
+             " per SM), " + (p.tma ? std::string("TMA sweeps, 64x16 tiles") : "cells per lane " + std::to_string(p.cx)) +
+             ", teams by " + (p.expo < 0 ? std::string("measured work") : "n^" + std::to_string(p.expo).substr(0, 4)) +
+             ":";
   for (int k = 0; k < count; ++k) bt->desc += " " + std::to_string(p.teams[k]);
   if (!times.empty()) bt->desc += "; autotune:" + times;
   *out = bt;

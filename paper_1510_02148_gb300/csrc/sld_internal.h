@@ -42,6 +42,8 @@ struct Geo {
 struct SolveArgs {
   Geo g;
   int cx;                 // cells per lane in x (1 or 4)
+  int vp;                 // row pitch (cells) of the inner vectors and inner faces
+  int64_t vpxy;           // vp * ny: plane pitch
   int ntx, nty;           // column tiles in x and y
   int64_t ntiles;         // ntx * nty * nz plane-tiles
   int d;                  // label columns of Z
@@ -88,6 +90,9 @@ struct sld_system_s {
   int device = 0, nsm = 0;
   cudaStream_t stream = nullptr;
   sld::Geo g{};
+  int nxp = 0;  // nx rounded up to 8: row pitch of the FP32/BF16 inner arrays and 16-bit labels
+  int64_t np = 0;  // nxp * ny * nz
+  int64_t nvec = 0;  // doubles allocated for each inner vector (z, p0, p1, xhat)
   int bc_type[6]{};
   double bc_value[6]{};
   // FP64 operator (assembled) and the permeability
@@ -147,8 +152,17 @@ cudaError_t launch_restrict(sld_system s, const double* v, double* out);
 cudaError_t launch_residual(sld_system s, const double* b, const double* x, double* partial_out,
                             double* rr_host, double* bb_host);
 // sld_solve_tma.cu
-bool tma_eligible(const Geo& g);
+bool tma_eligible(const Geo& g, bool fp64);
 int launch_solve_tma(sld_system s, SolveArgs& a, const sld_options& o, float* ms, std::string* msg);
+// batched FP32-inner solve on the TMA sweeps
+unsigned tma_batch_args_off(int dmax, bool wacc);
+size_t tma_batch_smem(int dmax, bool wacc);
+int tma_batch_occupancy(bool wacc, size_t smem);
+void tma_batch_tiles(SolveArgs* a);
+size_t tma_maps_bytes();
+bool tma_batch_maps(const SolveArgs& a, void* out);  // host memory, tma_maps_bytes() bytes
+cudaError_t tma_batch_launch(int G, size_t smem, unsigned args_off, bool wacc, const SolveArgs* d_args,
+                             const void* d_maps, const int* d_cta, cudaStream_t st);
 // sld_solve_tma_learned.cu (extra dense deflation columns)
 int launch_solve_tma_learned(sld_system s, SolveArgs& a, const sld_options& o, float* ms, std::string* msg);
 // sld_api.cu: the thread-local message returned by sld_last_error()
@@ -164,6 +178,9 @@ struct BatchPlan {
   int count = 0, G = 0, cx = 1, per_sm = 0;
   double expo = 1.0;
   bool fp64 = false, wacc = true;
+  bool tma = false;        // TMA sweeps (FP32 inner), else the register/shuffle sweeps
+  unsigned args_off = 0;   // TMA: shared-memory offset of the copied arguments
+  void* d_maps = nullptr;  // TMA: one set of tensor maps per system (device)
   size_t smem = 0;
   SolveArgs* d_args = nullptr;
   int* d_cta = nullptr;

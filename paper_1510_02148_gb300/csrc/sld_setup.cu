@@ -365,50 +365,57 @@ __global__ void k_learned_Efull(int d, int k, const double* __restrict__ E, cons
   Ef[t] = v;
 }
 
-template <typename Tout>
-__global__ void k_convert(int64_t n, const double* __restrict__ a, Tout* __restrict__ o) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) o[i] = (Tout)a[i];
-}
-
 // BF16 inner operator: each face rounded to nearest BF16, and the FP32
 // inverse of the quantized operator's diagonal (the sum of the six rounded
 // faces, in the order -z, -y, -x, +x, +y, +z, as the sweeps add them), 1 for
 // a Dirichlet cell.  The quantized operator is again a weighted Laplacian with
 // the Dirichlet couplings, so it stays symmetric positive definite.
-__global__ void k_quantize_bf16(Geo g, const double* __restrict__ Tx, const double* __restrict__ Ty,
+// Cell i = (iz * ny + iy) * nx + ix of the padded-row arrays sits at
+// (iz * ny + iy) * nxp + ix.
+__device__ __forceinline__ int64_t padded(const Geo& g, int nxp, int64_t i) {
+  return i + (i / g.nx) * (int64_t)(nxp - g.nx);
+}
+
+__global__ void k_quantize_bf16(Geo g, int nxp, const double* __restrict__ Tx, const double* __restrict__ Ty,
                                 const double* __restrict__ Tz, __nv_bfloat16* __restrict__ Tx16,
                                 __nv_bfloat16* __restrict__ Ty16, __nv_bfloat16* __restrict__ Tz16,
                                 float* __restrict__ invd) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= g.n) return;
   const int ix = (int)(i % g.nx), iy = (int)((i / g.nx) % g.ny), iz = (int)(i / g.nxy);
+  const int64_t ip = padded(g, nxp, i);
   auto q = [](double t) { return __double2bfloat16(t); };
   const __nv_bfloat16 px = q(Tx[i]), py = q(Ty[i]), pz = q(Tz[i]);
-  Tx16[i] = px;
-  Ty16[i] = py;
-  Tz16[i] = pz;
+  Tx16[ip] = px;
+  Ty16[ip] = py;
+  Tz16[ip] = pz;
   if (dir_axis(ix, g.nx, g.dlo_x, g.dhi_x) || dir_axis(iy, g.ny, g.dlo_y, g.dhi_y) ||
       dir_axis(iz, g.nz, g.dlo_z, g.dhi_z)) {
-    invd[i] = 1.0f;
+    invd[ip] = 1.0f;
     return;
   }
   const float mz = iz > 0 ? __bfloat162float(q(Tz[i - g.nxy])) : 0.0f;
   const float my = iy > 0 ? __bfloat162float(q(Ty[i - g.nx])) : 0.0f;
   const float mx = ix > 0 ? __bfloat162float(q(Tx[i - 1])) : 0.0f;
   const float dsum = ((((mz + my) + mx) + __bfloat162float(px)) + __bfloat162float(py)) + __bfloat162float(pz);
-  invd[i] = 1.0f / dsum;
+  invd[ip] = 1.0f / dsum;
 }
 
-__global__ void k_widen_bf16(int64_t n, const __nv_bfloat16* __restrict__ a, double* __restrict__ o) {
+__global__ void k_widen_bf16(Geo g, int nxp, const __nv_bfloat16* __restrict__ a, double* __restrict__ o) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) o[i] = (double)__bfloat162float(a[i]);
+  if (i < g.n) o[i] = (double)__bfloat162float(a[padded(g, nxp, i)]);
+}
+
+// FP32 inner faces, rounded to nearest, at the padded row pitch.
+__global__ void k_to_f32_padded(Geo g, int nxp, const double* __restrict__ a, float* __restrict__ o) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < g.n) o[padded(g, nxp, i)] = (float)a[i];
 }
 
 // 16-bit copy of the labels (d <= 65535), streamed by the TMA sweeps.
-__global__ void k_convert_labels(int64_t n, const int32_t* __restrict__ a, uint16_t* __restrict__ o) {
+__global__ void k_convert_labels(Geo g, int nxp, const int32_t* __restrict__ a, uint16_t* __restrict__ o) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) o[i] = (uint16_t)a[i];
+  if (i < g.n) o[padded(g, nxp, i)] = (uint16_t)a[i];
 }
 
 // y = A x, FP64, one thread per cell.
@@ -652,29 +659,29 @@ cudaError_t launch_learned_setup(sld_system s, const void* Zextra_dev, int k, in
 
 cudaError_t launch_quantize_fp32(sld_system s) {
   const int64_t n = s->g.n;
-  k_convert<float><<<blocks_for(n, 256), 256, 0, s->stream>>>(n, s->Tx, s->Tx32);
-  k_convert<float><<<blocks_for(n, 256), 256, 0, s->stream>>>(n, s->Ty, s->Ty32);
-  k_convert<float><<<blocks_for(n, 256), 256, 0, s->stream>>>(n, s->Tz, s->Tz32);
+  k_to_f32_padded<<<blocks_for(n, 256), 256, 0, s->stream>>>(s->g, s->nxp, s->Tx, s->Tx32);
+  k_to_f32_padded<<<blocks_for(n, 256), 256, 0, s->stream>>>(s->g, s->nxp, s->Ty, s->Ty32);
+  k_to_f32_padded<<<blocks_for(n, 256), 256, 0, s->stream>>>(s->g, s->nxp, s->Tz, s->Tz32);
   return cudaGetLastError();
 }
 
 cudaError_t launch_quantize_bf16(sld_system s) {
-  k_quantize_bf16<<<blocks_for(s->g.n, 256), 256, 0, s->stream>>>(s->g, s->Tx, s->Ty, s->Tz, s->Tx16, s->Ty16,
-                                                                 s->Tz16, s->invd16);
+  k_quantize_bf16<<<blocks_for(s->g.n, 256), 256, 0, s->stream>>>(s->g, s->nxp, s->Tx, s->Ty, s->Tz, s->Tx16,
+                                                                 s->Ty16, s->Tz16, s->invd16);
   return cudaGetLastError();
 }
 
 cudaError_t launch_widen_bf16(sld_system s, double* Tx, double* Ty, double* Tz) {
   const int64_t n = s->g.n;
-  k_widen_bf16<<<blocks_for(n, 256), 256, 0, s->stream>>>(n, s->Tx16, Tx);
-  k_widen_bf16<<<blocks_for(n, 256), 256, 0, s->stream>>>(n, s->Ty16, Ty);
-  k_widen_bf16<<<blocks_for(n, 256), 256, 0, s->stream>>>(n, s->Tz16, Tz);
+  k_widen_bf16<<<blocks_for(n, 256), 256, 0, s->stream>>>(s->g, s->nxp, s->Tx16, Tx);
+  k_widen_bf16<<<blocks_for(n, 256), 256, 0, s->stream>>>(s->g, s->nxp, s->Ty16, Ty);
+  k_widen_bf16<<<blocks_for(n, 256), 256, 0, s->stream>>>(s->g, s->nxp, s->Tz16, Tz);
   return cudaGetLastError();
 }
 
 cudaError_t launch_labels16(sld_system s) {
   const int64_t n = s->g.n;
-  k_convert_labels<<<blocks_for(n, 256), 256, 0, s->stream>>>(n, s->label, s->label16);
+  k_convert_labels<<<blocks_for(n, 256), 256, 0, s->stream>>>(s->g, s->nxp, s->label, s->label16);
   return cudaGetLastError();
 }
 

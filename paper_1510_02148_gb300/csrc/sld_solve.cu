@@ -129,7 +129,8 @@ struct Seg {
   bool own;   // an interior row (else a halo row)
   int xl;     // first cell of this lane
   int nv;     // valid cells of this lane (0 if the row is outside the grid)
-  int64_t rowbase;
+  int64_t rowbase;  // row start in cell order (labels, FP64 arrays)
+  int64_t rowp;     // row start at the inner arrays' pitch (vectors, inner faces)
 };
 
 template <int TX>
@@ -147,6 +148,7 @@ __device__ __forceinline__ Seg make_seg(const SolveArgs& a, int64_t ct, int z0, 
   const bool rowok = s.y >= 0 && s.y < a.g.ny;
   s.nv = rowok ? max(0, min(cx, a.g.nx - s.xl)) : 0;
   s.rowbase = (int64_t)s.y * a.g.nx + s.xl;
+  s.rowp = (int64_t)s.y * a.vp + s.xl;
   return s;
 }
 
@@ -193,7 +195,7 @@ __device__ void sweep_A(const SolveArgs& a, const Sm<T>& sm, const T* zb, const 
         for (int c = 0; c < CX; ++c) zv[c] = po[c] = T(0);
         return;
       }
-      const int64_t i = (int64_t)zz * g.nxy + sg.rowbase;
+      const int64_t i = (int64_t)zz * a.vpxy + sg.rowp;
       ld_cells<T, CX, false>(zb, i, sg.nv, zv);
       ld_cells<T, CX, false>(pold, i, sg.nv, po);
     };
@@ -206,10 +208,10 @@ __device__ void sweep_A(const SolveArgs& a, const Sm<T>& sm, const T* zb, const 
         }
         return;
       }
-      const int64_t i = (int64_t)zz * g.nxy + sg.rowbase;
-      ld_cells<T, CX, true>(Fx, i, sg.nv, f.fx);
-      ld_cells<T, CX, true>(Fy, i, sg.nv, f.fy);
-      ld_cells<T, CX, true>(Fz, i, sg.nv, f.fz);
+      const int64_t i = (int64_t)zz * g.nxy + sg.rowbase, ip = (int64_t)zz * a.vpxy + sg.rowp;
+      ld_cells<T, CX, true>(Fx, ip, sg.nv, f.fx);
+      ld_cells<T, CX, true>(Fy, ip, sg.nv, f.fy);
+      ld_cells<T, CX, true>(Fz, ip, sg.nv, f.fz);
       ld_labels<CX>(a.label, i, sg.nv, f.lb);
       if constexpr (sizeof(T) == 8) {
         ld_cells<T, CX, true>(a.diag64, i, sg.nv, f.dg);
@@ -224,7 +226,7 @@ __device__ void sweep_A(const SolveArgs& a, const Sm<T>& sm, const T* zb, const 
         for (int c = 0; c < CX; ++c) o[c] = T(0);
         return;
       }
-      ld_cells<T, CX, true>(Fy, (int64_t)zz * g.nxy + sg.rowbase, sg.nv, o);
+      ld_cells<T, CX, true>(Fy, (int64_t)zz * a.vpxy + sg.rowp, sg.nv, o);
     };
     // x-halo values of plane zz: lane 0 the cell left of the tile (z, p_old,
     // and the face between), lane 31 the cell right of it
@@ -233,7 +235,7 @@ __device__ void sweep_A(const SolveArgs& a, const Sm<T>& sm, const T* zb, const 
     auto ld_xh = [&](int zz, T& zx, T& px, T& fxl) {
       zx = px = fxl = T(0);
       if (zz < 0 || zz >= g.nz) return;
-      const int64_t row = (int64_t)zz * g.nxy + (int64_t)sg.y * g.nx;
+      const int64_t row = (int64_t)zz * a.vpxy + (int64_t)sg.y * a.vp;
       if (hl_ok) {
         zx = zb[row + sg.x0 - 1];
         px = pold[row + sg.x0 - 1];
@@ -284,7 +286,7 @@ __device__ void sweep_A(const SolveArgs& a, const Sm<T>& sm, const T* zb, const 
       T* sP = sm.P + buf * (kTY + 2) * RS;
       T* sTy = sm.Ty + buf * (kTY + 1) * TX;
       T* sTxh = sm.Txh + buf * kTY;
-      const int64_t iz = (int64_t)z * g.nxy + sg.rowbase;
+      const int64_t iz = (int64_t)z * a.vpxy + sg.rowp;
       if (sg.own) {
         // prefetch: plane z+2 vectors, plane z+1 faces and x-halo values
         ld_raw(z + 2, zv2, po2);
@@ -414,9 +416,8 @@ __device__ void sweep_B(const SolveArgs& a, const Sm<T>& sm, const T* p, T* zb, 
         }
         return;
       }
-      const int64_t i = (int64_t)zz * g.nxy + sg.rowbase;
-      ld_cells<T, CX, false>(p, i, sg.nv, pv);
-      ld_labels<CX>(a.label, i, sg.nv, lb);
+      ld_cells<T, CX, false>(p, (int64_t)zz * a.vpxy + sg.rowp, sg.nv, pv);
+      ld_labels<CX>(a.label, (int64_t)zz * g.nxy + sg.rowbase, sg.nv, lb);
     };
     auto mk_u = [&](const T(&pv)[CX], const int(&lb)[CX], T(&u)[CX]) {
 #pragma unroll
@@ -428,13 +429,13 @@ __device__ void sweep_B(const SolveArgs& a, const Sm<T>& sm, const T* p, T* zb, 
         for (int c = 0; c < CX; ++c) f.fx[c] = f.fy[c] = f.fz[c] = f.dg[c] = f.idg[c] = f.zo[c] = f.xo[c] = T(0);
         return;
       }
-      const int64_t i = (int64_t)zz * g.nxy + sg.rowbase;
-      ld_cells<T, CX, true>(Fx, i, sg.nv, f.fx);
-      ld_cells<T, CX, true>(Fy, i, sg.nv, f.fy);
-      ld_cells<T, CX, true>(Fz, i, sg.nv, f.fz);
+      const int64_t i = (int64_t)zz * g.nxy + sg.rowbase, ip = (int64_t)zz * a.vpxy + sg.rowp;
+      ld_cells<T, CX, true>(Fx, ip, sg.nv, f.fx);
+      ld_cells<T, CX, true>(Fy, ip, sg.nv, f.fy);
+      ld_cells<T, CX, true>(Fz, ip, sg.nv, f.fz);
       if (sg.own) {
-        ld_cells<T, CX, false>(zb, i, sg.nv, f.zo);
-        ld_cells<T, CX, false>(xh, i, sg.nv, f.xo);
+        ld_cells<T, CX, false>(zb, ip, sg.nv, f.zo);
+        ld_cells<T, CX, false>(xh, ip, sg.nv, f.xo);
       }
       if constexpr (sizeof(T) == 8) {
         ld_cells<T, CX, true>(a.diag64, i, sg.nv, f.dg);
@@ -450,7 +451,7 @@ __device__ void sweep_B(const SolveArgs& a, const Sm<T>& sm, const T* p, T* zb, 
         for (int c = 0; c < CX; ++c) o[c] = T(0);
         return;
       }
-      ld_cells<T, CX, true>(Fy, (int64_t)zz * g.nxy + sg.rowbase, sg.nv, o);
+      ld_cells<T, CX, true>(Fy, (int64_t)zz * a.vpxy + sg.rowp, sg.nv, o);
     };
     const bool hl_ok = sg.own && lane == 0 && sg.x0 - 1 >= 0 && sg.y < g.ny;
     const bool hr_ok = sg.own && lane == 31 && sg.x0 + TX < g.nx && sg.y < g.ny;
@@ -460,12 +461,13 @@ __device__ void sweep_B(const SolveArgs& a, const Sm<T>& sm, const T* p, T* zb, 
       fxl = T(0);
       if (zz < 0 || zz >= g.nz) return;
       const int64_t row = (int64_t)zz * g.nxy + (int64_t)sg.y * g.nx;
+      const int64_t rowp = (int64_t)zz * a.vpxy + (int64_t)sg.y * a.vp;
       if (hl_ok) {
-        px = p[row + sg.x0 - 1];
+        px = p[rowp + sg.x0 - 1];
         lx = __ldg(a.label + row + sg.x0 - 1);
-        fxl = __ldg(Fx + row + sg.x0 - 1);
+        fxl = __ldg(Fx + rowp + sg.x0 - 1);
       } else if (hr_ok) {
-        px = p[row + sg.x0 + TX];
+        px = p[rowp + sg.x0 + TX];
         lx = __ldg(a.label + row + sg.x0 + TX);
       }
     };
@@ -510,7 +512,7 @@ __device__ void sweep_B(const SolveArgs& a, const Sm<T>& sm, const T* p, T* zb, 
       T* sP = sm.P + buf * (kTY + 2) * RS;
       T* sTy = sm.Ty + buf * (kTY + 1) * TX;
       T* sTxh = sm.Txh + buf * kTY;
-      const int64_t iz = (int64_t)z * g.nxy + sg.rowbase;
+      const int64_t iz = (int64_t)z * a.vpxy + sg.rowp;
       if (sg.own) {
         ld_raw(z + 2, p2, l2);
         ld_faces(z + 1, F1);
@@ -705,6 +707,10 @@ void fill_args(sld_system s, const double* b_dev, const sld_options& o, SolveArg
   a.ntx = (s->g.nx + TX - 1) / TX;
   a.nty = (s->g.ny + kTY - 1) / kTY;
   a.ntiles = (int64_t)a.ntx * a.nty * s->g.nz;
+  // inner vectors and inner faces: rows padded to s->nxp cells in the FP32
+  // and BF16 forms (TMA boxes need 16-byte row strides); FP64 form unpadded
+  a.vp = fp64 ? s->g.nx : s->nxp;
+  a.vpxy = (int64_t)a.vp * s->g.ny;
   a.d = s->d;
   a.kL = s->kL;
   a.dk = s->d + s->kL;
@@ -771,19 +777,19 @@ int run_solve(sld_system s, const double* b_dev, const sld_options& o, sld_resul
   fill_args(s, b_dev, o, &a);
   // x = 0; the inner state is set by the first refinement step
   cudaMemsetAsync(s->x, 0, sizeof(double) * n, s->stream);
-  cudaMemsetAsync(s->xh, 0, sizeof(double) * n, s->stream);
+  cudaMemsetAsync(s->xh, 0, sizeof(double) * s->nvec, s->stream);
   cudaMemsetAsync(s->bar, 0, 64, s->stream);
   cudaMemsetAsync(s->out, 0, sizeof(double) * kOutCount, s->stream);
   float ms = 0.f;
   int st;
   const bool wacc = s->d <= kWarpAccMaxD;
   const char* force = std::getenv("SLD_SOLVER_PATH");
-  const bool use_tma = tma_eligible(s->g) && !(force && std::strcmp(force, "generic") == 0);
+  const bool use_tma = tma_eligible(s->g, fp64) && !(force && std::strcmp(force, "generic") == 0);
   if (bf16 && !use_tma) {
-    *msg = "BF16 coefficients are streamed by the TMA sweeps only: they need nx % 8 == 0";
+    *msg = "BF16 coefficients are streamed by the TMA sweeps only";
     return SLD_ERR_INVALID_ARG;
   }
-  if (s->kL > 0 && (!use_tma || bf16)) {
+  if (s->kL > 0 && (!use_tma || bf16 || s->g.nx % 8 != 0)) {
     *msg = "extra dense deflation vectors need the TMA sweeps (nx % 8 == 0) and SLD_FP64 or SLD_FP32_IR";
     return SLD_ERR_INVALID_ARG;
   }
@@ -830,7 +836,8 @@ namespace {
 template <typename T, int CX, bool WACC>
 int batch_capture(sld_system s0, BatchPlan* p, sld_system* sys, std::string* msg) {
   auto kern = k_solve_batch<T, CX, WACC>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem);
+  cudaError_t e = p->tma ? cudaSuccess
+                         : cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem);
   if (e != cudaSuccess) {
     *msg = std::string("batch kernel attribute: ") + cudaGetErrorString(e);
     return SLD_ERR_CUDA;
@@ -845,24 +852,29 @@ int batch_capture(sld_system s0, BatchPlan* p, sld_system* sys, std::string* msg
   for (int k = 0; k < p->count; ++k) {
     sld_system s = sys[k];
     cudaMemsetAsync(s->x, 0, sizeof(double) * s->g.n, st);
-    cudaMemsetAsync(s->xh, 0, sizeof(double) * s->g.n, st);
+    cudaMemsetAsync(s->xh, 0, sizeof(double) * s->nvec, st);
     cudaMemsetAsync(s->bar, 0, 64, st);
     cudaMemsetAsync(s->out, 0, sizeof(double) * kOutCount, st);
     cudaMemsetAsync(s->status, 0, sizeof(int) * 4, st);
   }
-  cudaLaunchConfig_t cfg{};
-  cfg.gridDim = dim3(p->G);
-  cfg.blockDim = dim3(kThreads);
-  cfg.dynamicSmemBytes = p->smem;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeCooperative;
-  attr[0].val.cooperative = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  const SolveArgs* da = p->d_args;
-  const int* dc = p->d_cta;
-  cudaError_t el = cudaLaunchKernelEx(&cfg, kern, da, dc);
+  cudaError_t el;
+  if (p->tma) {
+    el = tma_batch_launch(p->G, p->smem, p->args_off, p->wacc, p->d_args, p->d_maps, p->d_cta, st);
+  } else {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(p->G);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = p->smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const SolveArgs* da = p->d_args;
+    const int* dc = p->d_cta;
+    el = cudaLaunchKernelEx(&cfg, kern, da, dc);
+  }
   e = cudaStreamEndCapture(st, &p->graph);
   if (el != cudaSuccess || e != cudaSuccess) {
     *msg = std::string("batch capture: ") + cudaGetErrorString(el != cudaSuccess ? el : e);
@@ -897,6 +909,8 @@ void batch_free(BatchPlan* p) {
   if (p->graph) cudaGraphDestroy(p->graph);
   if (p->d_args) cudaFree(p->d_args);
   if (p->d_cta) cudaFree(p->d_cta);
+  if (p->d_maps) cudaFree(p->d_maps);
+  p->d_maps = nullptr;
   p->exec = nullptr;
   p->graph = nullptr;
   p->d_args = nullptr;
@@ -923,8 +937,18 @@ int batch_build(sld_system* sys, int count, const sld_options& o, int per_sm, do
                       : (p->wacc ? FN<double, 1, true>(__VA_ARGS__) : FN<double, 1, false>(__VA_ARGS__))) \
            : (cx == 4 ? (p->wacc ? FN<float, 4, true>(__VA_ARGS__) : FN<float, 4, false>(__VA_ARGS__))   \
                       : (p->wacc ? FN<float, 1, true>(__VA_ARGS__) : FN<float, 1, false>(__VA_ARGS__))))
-  p->smem = SLD_BATCH_DISPATCH(batch_smem, dmax);
-  int occ = SLD_BATCH_DISPATCH(batch_occupancy, p->smem);
+  // the FP32-inner batch runs on the TMA sweeps; the FP64 one on the
+  // register/shuffle sweeps (the FP64 operator's rows are not padded)
+  p->tma = !p->fp64 && tma_eligible(s0->g, false);
+  int occ;
+  if (p->tma) {
+    p->args_off = tma_batch_args_off(dmax, p->wacc);
+    p->smem = tma_batch_smem(dmax, p->wacc);
+    occ = tma_batch_occupancy(p->wacc, p->smem);
+  } else {
+    p->smem = SLD_BATCH_DISPATCH(batch_smem, dmax);
+    occ = SLD_BATCH_DISPATCH(batch_occupancy, p->smem);
+  }
   if (occ < 1) {
     *msg = "batch kernel does not fit on an SM";
     return SLD_ERR_CUDA;
@@ -942,11 +966,15 @@ int batch_build(sld_system* sys, int count, const sld_options& o, int per_sm, do
   for (int k = 0; k < count; ++k) {
     fill_args(sys[k], sys[k]->bwork, o, &args[k]);
     SolveArgs& a = args[k];
-    a.cx = cx;
-    const int TX = 32 * cx;
-    a.ntx = (a.g.nx + TX - 1) / TX;
-    a.nty = (a.g.ny + kTY - 1) / kTY;
-    a.ntiles = (int64_t)a.ntx * a.nty * a.g.nz;
+    if (p->tma) {
+      tma_batch_tiles(&a);
+    } else {
+      a.cx = cx;
+      const int TX = 32 * cx;
+      a.ntx = (a.g.nx + TX - 1) / TX;
+      a.nty = (a.g.ny + kTY - 1) / kTY;
+      a.ntiles = (int64_t)a.ntx * a.nty * a.g.nz;
+    }
     cap[k] = (int)std::min<int64_t>(std::min<int64_t>(a.ntiles, sys[k]->part_rows), G);
     w[k] = weights ? std::max(weights[k], 1e-30) : std::pow((double)a.g.n, expo);
     wsum += w[k];
@@ -987,6 +1015,16 @@ int batch_build(sld_system* sys, int count, const sld_options& o, int per_sm, do
   }
   cudaError_t e = cudaMalloc(&p->d_args, sizeof(SolveArgs) * count);
   if (e == cudaSuccess) e = cudaMalloc(&p->d_cta, sizeof(int) * used);
+  if (e == cudaSuccess && p->tma) {
+    std::vector<unsigned char> maps(tma_maps_bytes() * count);
+    for (int k = 0; k < count; ++k)
+      if (!tma_batch_maps(args[k], maps.data() + tma_maps_bytes() * k)) {
+        *msg = "batch: tensor map creation failed";
+        return SLD_ERR_CUDA;
+      }
+    e = cudaMalloc(&p->d_maps, maps.size());
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_maps, maps.data(), maps.size(), cudaMemcpyHostToDevice);
+  }
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(p->d_args, args.data(), sizeof(SolveArgs) * count, cudaMemcpyHostToDevice, stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(p->d_cta, cta_sys.data(), sizeof(int) * used, cudaMemcpyHostToDevice, stream);

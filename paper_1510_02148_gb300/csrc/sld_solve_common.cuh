@@ -182,6 +182,12 @@ __device__ __forceinline__ T stencil(bool dirc, T u, T dg, T fxm, T xm, bool mxm
   }
 }
 
+// Index of cell i (cell order, unpadded rows) in the inner vectors, whose
+// rows are a.vp cells long.
+__device__ __forceinline__ int64_t vidx(const SolveArgs& a, int64_t i) {
+  return a.vp == a.g.nx ? i : i + (i / a.g.nx) * (int64_t)(a.vp - a.g.nx);
+}
+
 // ---------------------------------------------------------------------------
 // Refinement sweeps (FP64, one thread per cell).
 // ---------------------------------------------------------------------------
@@ -228,7 +234,7 @@ __device__ void sweep_O1(const SolveArgs& a, double* sacc, double* red, double* 
     int l = -1;
     if (ok) {
       const int ix = (int)(i % g.nx), iy = (int)((i / g.nx) % g.ny), iz = (int)(i / g.nxy);
-      const double Aw = apply64(a, i, ix, iy, iz, [&](int64_t j) { return a.x[j] + (double)xh[j]; });
+      const double Aw = apply64(a, i, ix, iy, iz, [&](int64_t j) { return a.x[j] + (double)xh[vidx(a, j)]; });
       const double bi = a.b[i];
       r = bi - Aw;
       a.r64[i] = r;
@@ -281,12 +287,13 @@ __device__ void sweep_O2(const SolveArgs& a, const double* Yd, double* red, doub
       Zy += (double)a.ZL32[i * kMaxL + j] * yj;
     }
     const double rh = a.r64[i] - AZy;
-    a.x[i] = a.x[i] + (double)xh[i] + Zy;
-    const T zt = (T)(rh * (a.invdi ? (double)a.invdi[i] : a.invdiag64[i]));
-    zb[i] = zt;
-    xh[i] = T(0);
-    p0[i] = T(0);
-    p1[i] = T(0);
+    const int64_t ip = vidx(a, i);
+    a.x[i] = a.x[i] + (double)xh[ip] + Zy;
+    const T zt = (T)(rh * (a.invdi ? (double)a.invdi[ip] : a.invdiag64[i]));
+    zb[ip] = zt;
+    xh[ip] = T(0);
+    p0[ip] = T(0);
+    p1[ip] = T(0);
     rr += rh * rh;
     rho += rh * (double)zt;
   }

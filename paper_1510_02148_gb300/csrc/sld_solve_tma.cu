@@ -5,8 +5,10 @@
 namespace sld {
 
 // Row strides must be multiples of 16 bytes for every streamed array (the
-// 16-bit labels are the narrowest): nx % 8 == 0.
-bool tma_eligible(const Geo& g) { return g.nx % 8 == 0 && encode_fn() != nullptr; }
+// 16-bit labels are the narrowest): the FP32 and BF16 forms keep their inner
+// arrays and labels at rows padded to 8 cells, so any grid qualifies; the
+// FP64 form streams the unpadded FP64 operator: nx % 8 == 0.
+bool tma_eligible(const Geo& g, bool fp64) { return (!fp64 || g.nx % 8 == 0) && encode_fn() != nullptr; }
 
 int launch_solve_tma(sld_system s, SolveArgs& a, const sld_options& o, float* ms, std::string* msg) {
   if (a.kL > 0) return launch_solve_tma_learned(s, a, o, ms, msg);
@@ -21,6 +23,53 @@ int launch_solve_tma(sld_system s, SolveArgs& a, const sld_options& o, float* ms
   // tiles with 4- or 5-deep rings on the 256 x 256 x 128 workload)
   return wacc ? launch_tma<float, float, 16, 3, true, false>(s, a, o, ms, msg)
               : launch_tma<float, float, 16, 3, false, false>(s, a, o, ms, msg);
+}
+
+// ---------------------------------------------------------------------------
+// Batched FP32-inner solve on the TMA sweeps (64 x 16 tiles, 3-deep ring).
+// ---------------------------------------------------------------------------
+unsigned tma_batch_args_off(int dmax, bool wacc) {
+  const size_t b = wacc ? tma_smem_bytes<float, float, 16, 3, true>(dmax, dmax)
+                        : tma_smem_bytes<float, float, 16, 3, false>(dmax, dmax);
+  return (unsigned)((b + 15) / 16 * 16);
+}
+
+size_t tma_batch_smem(int dmax, bool wacc) { return tma_batch_args_off(dmax, wacc) + sizeof(SolveArgs); }
+
+int tma_batch_occupancy(bool wacc, size_t smem) {
+  const void* kern = wacc ? (const void*)k_solve_tma_batch<float, float, 16, 3, true>
+                          : (const void*)k_solve_tma_batch<float, float, 16, 3, false>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int per = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 256, smem);
+  return per;
+}
+
+void tma_batch_tiles(SolveArgs* a) {
+  a->ntx = (a->g.nx + kTX - 1) / kTX;
+  a->nty = (a->g.ny + 16 - 1) / 16;
+  a->ntiles = (int64_t)a->ntx * a->nty * a->g.nz;
+}
+
+size_t tma_maps_bytes() { return sizeof(Maps); }
+
+bool tma_batch_maps(const SolveArgs& a, void* out) { return build_maps<float, float, 16>(a, static_cast<Maps*>(out)); }
+
+cudaError_t tma_batch_launch(int G, size_t smem, unsigned args_off, bool wacc, const SolveArgs* d_args,
+                             const void* d_maps, const int* d_cta, cudaStream_t st) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(G);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const Maps* mp = static_cast<const Maps*>(d_maps);
+  if (wacc) return cudaLaunchKernelEx(&cfg, k_solve_tma_batch<float, float, 16, 3, true>, d_args, mp, d_cta, args_off);
+  return cudaLaunchKernelEx(&cfg, k_solve_tma_batch<float, float, 16, 3, false>, d_args, mp, d_cta, args_off);
 }
 
 }  // namespace sld

@@ -435,7 +435,9 @@ __device__ bool sweep_tma(const SolveArgs& a, const Maps& mp, const Ring<S>& rg,
       const bool dzc = dir_axis(z, g.nz, g.dlo_z, g.dhi_z);
       const bool dzm = dir_axis(z - 1, g.nz, g.dlo_z, g.dhi_z);
       const bool dzp = dir_axis(z + 1, g.nz, g.dlo_z, g.dhi_z);
-      const int64_t iz = (int64_t)z * g.nxy + (int64_t)y * g.nx + xl;
+      // this thread's cells in the inner vectors (rows a.vp long; extra
+      // deflation columns need a.vp == nx)
+      const int64_t iz = (int64_t)z * a.vpxy + (int64_t)y * a.vp + xl;
       if constexpr (IS_A) {
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
@@ -585,9 +587,8 @@ __host__ __device__ constexpr size_t tma_smem_bytes(int d, int dk) {
 }
 
 template <typename T, typename F, int TY, int S, bool WACC, bool LRN>
-__global__ void __launch_bounds__(16 * TY) k_solve_tma(SolveArgs a, const __grid_constant__ Maps mp, int ntx) {
+__device__ __forceinline__ void tma_body(const SolveArgs& a, const Maps& mp, int ntx, unsigned char* smem_raw) {
   using C = TCfg<T, F, TY>;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
   Ring<S> rg;
   rg.slots = smem_raw;
   rg.slot_bytes = C::SLOT;
@@ -626,6 +627,28 @@ __global__ void __launch_bounds__(16 * TY) k_solve_tma(SolveArgs a, const __grid
       });
 }
 
+template <typename T, typename F, int TY, int S, bool WACC, bool LRN>
+__global__ void __launch_bounds__(16 * TY) k_solve_tma(SolveArgs a, const __grid_constant__ Maps mp, int ntx) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  tma_body<T, F, TY, S, WACC, LRN>(a, mp, ntx, smem_raw);
+}
+
+// Batched solve: CTA c works on system cta_sys[c] with the team of CTAs the
+// host assigned to it.  Its arguments are copied into shared memory (at
+// args_off, past the solve's own layout); its tensor maps stay in global
+// memory, where the TMA unit reads them.
+template <typename T, typename F, int TY, int S, bool WACC>
+__global__ void __launch_bounds__(16 * TY) k_solve_tma_batch(const SolveArgs* __restrict__ all,
+                                                           const Maps* __restrict__ maps,
+                                                           const int* __restrict__ cta_sys, unsigned args_off) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  SolveArgs* as = reinterpret_cast<SolveArgs*>(smem_raw + args_off);
+  const int k = cta_sys[blockIdx.x];
+  if (threadIdx.x == 0) *as = all[k];
+  __syncthreads();
+  tma_body<T, F, TY, S, WACC, false>(*as, maps[k], as->ntx, smem_raw);
+}
+
 // ---------------------------------------------------------------------------
 // Host side: tensor maps and the launch.
 // ---------------------------------------------------------------------------
@@ -641,11 +664,13 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-bool make_map(CUtensorMap* m, CUtensorMapDataType dt, size_t es, const void* ptr, const Geo& g, int bx, int by) {
+// A map over nx x ny x nz cells stored with rows of `pitch` cells.
+bool make_map(CUtensorMap* m, CUtensorMapDataType dt, size_t es, const void* ptr, const Geo& g, int pitch, int bx,
+              int by) {
   auto fn = encode_fn();
   if (!fn) return false;
   cuuint64_t dims[3] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz};
-  cuuint64_t strides[2] = {(cuuint64_t)g.nx * es, (cuuint64_t)g.nxy * es};
+  cuuint64_t strides[2] = {(cuuint64_t)pitch * es, (cuuint64_t)pitch * g.ny * es};
   cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
   cuuint32_t estr[3] = {1, 1, 1};
   return fn(m, dt, 3, const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -661,24 +686,24 @@ bool build_maps(const SolveArgs& a, Maps* mp) {
   const size_t es = sizeof(T), ef = sizeof(F);
   const Geo& g = a.g;
   bool ok = true;
-  ok = ok && make_map(&mp->zb_h, dt, es, a.z, g, C::WH, TY + 2);
-  ok = ok && make_map(&mp->p_h[0], dt, es, a.p0, g, C::WH, TY + 2);
-  ok = ok && make_map(&mp->p_h[1], dt, es, a.p1, g, C::WH, TY + 2);
-  ok = ok && make_map(&mp->fx, df, ef, a.Txi, g, C::WF, TY);
-  ok = ok && make_map(&mp->fy, df, ef, a.Tyi, g, kTX, TY + 1);
-  ok = ok && make_map(&mp->fz, df, ef, a.Tzi, g, kTX, TY);
-  ok = ok && make_map(&mp->lb_o, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, a.label16, g, kTX, TY);
-  ok = ok && make_map(&mp->lb_h, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, a.label16, g, C::WL, TY + 2);
-  ok = ok && make_map(&mp->zb_o, dt, es, a.z, g, kTX, TY);
-  ok = ok && make_map(&mp->xh_o, dt, es, a.xh, g, kTX, TY);
+  ok = ok && make_map(&mp->zb_h, dt, es, a.z, g, a.vp, C::WH, TY + 2);
+  ok = ok && make_map(&mp->p_h[0], dt, es, a.p0, g, a.vp, C::WH, TY + 2);
+  ok = ok && make_map(&mp->p_h[1], dt, es, a.p1, g, a.vp, C::WH, TY + 2);
+  ok = ok && make_map(&mp->fx, df, ef, a.Txi, g, a.vp, C::WF, TY);
+  ok = ok && make_map(&mp->fy, df, ef, a.Tyi, g, a.vp, kTX, TY + 1);
+  ok = ok && make_map(&mp->fz, df, ef, a.Tzi, g, a.vp, kTX, TY);
+  ok = ok && make_map(&mp->lb_o, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, a.label16, g, a.vp, kTX, TY);
+  ok = ok && make_map(&mp->lb_h, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, a.label16, g, a.vp, C::WL, TY + 2);
+  ok = ok && make_map(&mp->zb_o, dt, es, a.z, g, a.vp, kTX, TY);
+  ok = ok && make_map(&mp->xh_o, dt, es, a.xh, g, a.vp, kTX, TY);
   if (C::kDiag) {
-    ok = ok && make_map(&mp->dg_o, dt, es, a.diag64, g, kTX, TY);
-    ok = ok && make_map(&mp->idg_o, dt, es, a.invdiag64, g, kTX, TY);
+    ok = ok && make_map(&mp->dg_o, dt, es, a.diag64, g, a.vp, kTX, TY);
+    ok = ok && make_map(&mp->idg_o, dt, es, a.invdiag64, g, a.vp, kTX, TY);
   } else {
     mp->dg_o = mp->zb_o;
     mp->idg_o = mp->zb_o;
   }
-  if (C::kScale) ok = ok && make_map(&mp->sc_o, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, a.invdi, g, kTX, TY);
+  if (C::kScale) ok = ok && make_map(&mp->sc_o, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, a.invdi, g, a.vp, kTX, TY);
   else mp->sc_o = mp->zb_o;
   return ok;
 }
