@@ -1,0 +1,79 @@
+"""Parity at the benchmark sizes, in the launch configuration bench.py times,
+checked through quantities the oracle computes at any size: the labels
+(bit-exact), and the FP64 true residual of the GPU solution evaluated with the
+oracle's own assembled matrix.  Plus the coarse sizes above the per-warp
+accumulator limit (d > 256) against the full oracle solve on a smaller grid."""
+import numpy as np
+import pytest
+
+from paper_1510_02148_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sld():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1510_02148_gb300 import _build, sld as mod
+    _build.build()
+    mod.load()
+    return mod
+
+
+def _true_relres(A, x):
+    return np.linalg.norm(A.b - A.spmv(x)) / np.linalg.norm(A.b)
+
+
+def test_lognormal_256x256x128(sld, oracle_mod):
+    """The bench workload (8.4M cells, d = 128), FP32 inner and plain FP64."""
+    import torch
+    P = W.lognormal_point_source()
+    s = sld.System(torch.from_numpy(P.K.reshape(-1)).cuda(), torch.from_numpy(P.q.reshape(-1)).cuda(),
+                   P.bc_type, P.bc_value, stream=torch.cuda.current_stream().cuda_stream, shape=P.shape)
+    lab = s.make_labels(P.S, P.tau, P.L)
+    assert np.array_equal(lab, oracle_mod.labels(P.K, P.S, P.tau, P.L))
+    s.build_deflation(P.d)
+    A = oracle_mod.assemble(P.K, P.q, P.bc_type, P.bc_value)
+    x32, i32 = s.solve(precision=sld.FP32_IR)
+    x64, i64 = s.solve(precision=sld.FP64)
+    for x, info in ((x32, i32), (x64, i64)):
+        t = _true_relres(A, x)
+        assert info.kernel_path == 1
+        assert t <= 1e-9 and abs(t - info.true_relres) <= 1e-3 * t + 1e-12, (t, info.true_relres)
+    s.close()
+
+
+def test_inclusions_512x512x256_bf16(sld, oracle_mod):
+    """The BF16-coefficient workload (67M cells, d = 1536: shared-atomic label sums)."""
+    import torch
+    P, _ = W.inclusion_field()
+    s = sld.System(torch.from_numpy(P.K.reshape(-1)).cuda(), None, P.bc_type, P.bc_value, shape=P.shape)
+    lab = s.make_labels(P.S, P.tau, P.L)
+    assert np.array_equal(lab, oracle_mod.labels(P.K, P.S, P.tau, P.L))
+    s.build_deflation(P.d)
+    x, info = s.solve(precision=sld.BF16COEF_IR)
+    A = oracle_mod.assemble(P.K, P.q, P.bc_type, P.bc_value)
+    t = _true_relres(A, x)
+    assert t <= 1e-9 and abs(t - info.true_relres) <= 1e-3 * t + 1e-12, (t, info.true_relres)
+    s.close()
+
+
+def test_large_d_parity(sld, oracle_mod):
+    """d = 512 label columns (above the per-warp accumulator limit of 256):
+    FP64 within 1e-7 of the oracle, iterations within 2; FP32 inner reaches 1e-9."""
+    P = W.lognormal_point_source(64, 64, 32, 8, (8, 8, 4), seed=6)
+    assert P.d == 512
+    A = oracle_mod.assemble(P.K, P.q, P.bc_type, P.bc_value)
+    lab = oracle_mod.labels(P.K, P.S, P.tau, P.L)
+    ref = oracle_mod.dpcg(A, lab, P.d, tol=P.tol)
+    s = sld.from_problem(P)
+    x, info = s.solve(precision=sld.FP64)
+    assert np.linalg.norm(x - ref.x) / np.linalg.norm(ref.x) <= 1e-7
+    assert abs(info.iterations - ref.iterations) <= 2
+    x32, i32 = s.solve(precision=sld.FP32_IR)
+    assert _true_relres(A, x32) <= 1e-9
+    with pytest.raises(sld.SldError, match="d must be"):
+        s.build_deflation(4097)
+    s.close()
