@@ -398,7 +398,7 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak,
                      "traffic": (TRAFFIC_RATIO_FP32 * alg_bytes if TRAFFIC_RATIO_FP32 else None),
-                     "kernel": "k_solve_tma<float,16,3,true> (persistent, cooperative)", "peak_kind": peak_kind},
+                     "kernel": "k_solve_tma<float, float, 16, 3, true, false> (persistent, cooperative)", "peak_kind": peak_kind},
         "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(Kh.numel() * 8 + qh.numel() * 8),
                 "d2h_bytes_per_step": int(xh.numel() * 8),
                 "what": "sld_build_system(host K, q) + make_labels + build_deflation + sld_solve -> host x"},
