@@ -38,11 +38,11 @@ BYTES_ITER_FP32 = 60   # A: z, p_old, 3 faces, label, p_new  B: p, label, 3 face
 BYTES_ITER_FP64 = 140  # same vectors and faces in FP64 + diag (A, B) and 1/diag (B)
 BYTES_OUTER = 152      # O1: x, xhat, b, faces, diag, label, r'  O2: r', label, faces, diag, x r/w, xhat r/w, 1/diag, z, p0, p1
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) over algorithmic
-# bytes of one launch of k_solve_tma<float, float, 16, 3, true>, from an ncu
-# capture of a 300-iteration launch on this workload (167.2 GB / 153.5 GB);
-# the traffic of a full launch is this ratio times its algorithmic bytes.
-# Must be re-measured (or set to None) whenever that kernel changes.
-TRAFFIC_RATIO_FP32 = 1.089
+# bytes of one launch of k_solve_tma<float, float, 8, 3, true, false>, from an
+# ncu capture of a 300-iteration launch on this workload; the traffic of a
+# full launch is this ratio times its algorithmic bytes.  Must be re-measured
+# (or set to None) whenever that kernel changes.
+TRAFFIC_RATIO_FP32 = 1.091
 
 
 def _peaks():
@@ -398,7 +398,7 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak,
                      "traffic": (TRAFFIC_RATIO_FP32 * alg_bytes if TRAFFIC_RATIO_FP32 else None),
-                     "kernel": "k_solve_tma<float, float, 16, 3, true, false> (persistent, cooperative)", "peak_kind": peak_kind},
+                     "kernel": "k_solve_tma<float, float, 8, 3, true, false> (persistent, cooperative)", "peak_kind": peak_kind},
         "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(Kh.numel() * 8 + qh.numel() * 8),
                 "d2h_bytes_per_step": int(xh.numel() * 8),
                 "what": "sld_build_system(host K, q) + make_labels + build_deflation + sld_solve -> host x"},

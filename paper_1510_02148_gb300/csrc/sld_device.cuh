@@ -23,6 +23,10 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
   return v;
 }
 
+__device__ __forceinline__ void red_release_add_u32(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 __device__ __forceinline__ int ld_volatile_i32(const int* p) {
   return *reinterpret_cast<const volatile int*>(p);
 }
@@ -40,8 +44,9 @@ __device__ __forceinline__ bool grid_barrier(const SyncArgs& sy, unsigned& epoch
     ++epoch;
     const unsigned target = epoch * (unsigned)sy.ncta;
     const bool skip = sy.skip_epoch > 0 && (int)blockIdx.x == sy.cta0 && epoch == (unsigned)sy.skip_epoch;
-    __threadfence();
-    if (!skip) atomicAdd(sy.count, 1u);
+    // release: the CTA's writes (ordered before this thread by the CTA
+    // barrier above) become visible before the arrival does
+    if (!skip) red_release_add_u32(sy.count, 1u);
     int ok = 1;
     const unsigned long long t0 = global_ns();
     unsigned spins = 0;
@@ -55,8 +60,10 @@ __device__ __forceinline__ bool grid_barrier(const SyncArgs& sy, unsigned& epoch
         }
       }
     }
-    __threadfence();
-    if (ok && ld_volatile_i32(sy.status) != 0) ok = 0;
+    // the acquire load that saw the count orders every later read of this
+    // CTA (through the CTA barrier below).  An error recorded elsewhere is
+    // seen by the bounded spin of a later barrier, which the failed CTA
+    // never reaches.
     s_ok = ok;
   }
   __syncthreads();

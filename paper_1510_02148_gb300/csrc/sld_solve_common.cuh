@@ -39,25 +39,6 @@ __device__ double block_sum(double v, double* red) {
   return t;
 }
 
-// Flush the per-lane run sums of a warp into the shared label accumulators.
-// Lanes are grouped by label; each group is summed in lane order and added
-// once by its lowest lane, so no two lanes of a warp write the same slot.
-template <bool WACC>
-__device__ __forceinline__ void warp_flush(int cur, double acc, double* sacc, int d, int warp) {
-  const int lane = threadIdx.x & 31;
-  const unsigned grp = __match_any_sync(kFull, cur);
-  double sum = 0.0;
-#pragma unroll 4
-  for (int src = 0; src < 32; ++src) {
-    const double v = __shfl_sync(kFull, acc, src);
-    if ((grp >> src) & 1u) sum += v;
-  }
-  if (cur >= 0 && lane == __ffs(grp) - 1) {
-    if constexpr (WACC) sacc[warp * d + cur] += sum;
-    else atomicAdd(&sacc[cur], sum);
-  }
-}
-
 // Per-lane accumulation of v into the label sums s = Z^T v.  Each lane keeps
 // a run sum for its current label; a change of label is a vote of the warp.
 //   L == 0 (labels of any form): every change flushes the runs warp-wide.
@@ -151,6 +132,21 @@ struct LabelAcc {
     }
     if (valid) run += v;
   }
+  // four consecutive cells of a lane (the first nv valid): the same as four
+  // add() calls, with one vote when every lane stays on its current label
+  __device__ __forceinline__ void add4(int nv, const int (&lab)[4], const T (&v)[4], double* sacc, int d, int warp) {
+    bool same = true;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) same = same && (c >= nv || lab[c] == curl);
+    if (__all_sync(kFull, same)) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        if (c < nv) run += v[c];
+    } else {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) add(c < nv, lab[c], v[c], sacc, d, warp);
+    }
+  }
 };
 
 // The 7-point operator at one free or Dirichlet cell.
@@ -182,12 +178,6 @@ __device__ __forceinline__ T stencil(bool dirc, T u, T dg, T fxm, T xm, bool mxm
   }
 }
 
-// Index of cell i (cell order, unpadded rows) in the inner vectors, whose
-// rows are a.vp cells long.
-__device__ __forceinline__ int64_t vidx(const SolveArgs& a, int64_t i) {
-  return a.vp == a.g.nx ? i : i + (i / a.g.nx) * (int64_t)(a.vp - a.g.nx);
-}
-
 // ---------------------------------------------------------------------------
 // Refinement sweeps (FP64, one thread per cell).
 // ---------------------------------------------------------------------------
@@ -196,45 +186,93 @@ __device__ __forceinline__ bool is_dir_cell(const Geo& g, int ix, int iy, int iz
          dir_axis(iz, g.nz, g.dlo_z, g.dhi_z);
 }
 
-// (A w)_i in FP64 for the vector given by `val(j)`.
+// Cells i0, i0 + stride, i0 + 2 stride, ... with their grid coordinates and
+// their index in the padded inner vectors, stepped by carries (one division
+// per thread and sweep instead of several per cell).
+struct CellWalk {
+  int64_t i, ip, stride, n;
+  int ix, iy, iz, sx, sy, sz, nx, ny, vp;
+  int64_t vpxy;
+  __device__ void init(const SolveArgs& a, int64_t i0, int64_t st) {
+    const Geo& g = a.g;
+    i = i0;
+    stride = st;
+    n = g.n;
+    nx = g.nx;
+    ny = g.ny;
+    vp = a.vp;
+    vpxy = a.vpxy;
+    ix = (int)(i0 % g.nx);
+    iy = (int)((i0 / g.nx) % g.ny);
+    iz = (int)(i0 / g.nxy);
+    sx = (int)(st % g.nx);
+    sy = (int)((st / g.nx) % g.ny);
+    sz = (int)(st / g.nxy);
+    ip = (int64_t)iz * vpxy + (int64_t)iy * vp + ix;
+  }
+  __device__ bool ok() const { return i < n; }
+  __device__ void next() {
+    i += stride;
+    ix += sx;
+    int c = 0;
+    if (ix >= nx) { ix -= nx; c = 1; }
+    iy += sy + c;
+    c = 0;
+    if (iy >= ny) { iy -= ny; c = 1; }
+    iz += sz + c;
+    ip = (int64_t)iz * vpxy + (int64_t)iy * vp + ix;
+  }
+};
+
+// (A w)_i in FP64 for the vector given by `val(j, jp)` (j: cell index, jp:
+// its index in the padded inner vectors) at the walk's cell.
 template <typename F>
-__device__ __forceinline__ double apply64(const SolveArgs& a, int64_t i, int ix, int iy, int iz, F val) {
+__device__ __forceinline__ double apply64(const SolveArgs& a, const CellWalk& c, F val) {
   const Geo& g = a.g;
-  if (is_dir_cell(g, ix, iy, iz)) return val(i);
-  double v = a.diag64[i] * val(i);
-  if (ix > 0 && !dir_axis(ix - 1, g.nx, g.dlo_x, g.dhi_x)) v -= a.Tx64[i - 1] * val(i - 1);
-  if (ix + 1 < g.nx && !dir_axis(ix + 1, g.nx, g.dlo_x, g.dhi_x)) v -= a.Tx64[i] * val(i + 1);
-  if (iy > 0 && !dir_axis(iy - 1, g.ny, g.dlo_y, g.dhi_y)) v -= a.Ty64[i - g.nx] * val(i - g.nx);
-  if (iy + 1 < g.ny && !dir_axis(iy + 1, g.ny, g.dlo_y, g.dhi_y)) v -= a.Ty64[i] * val(i + g.nx);
-  if (iz > 0 && !dir_axis(iz - 1, g.nz, g.dlo_z, g.dhi_z)) v -= a.Tz64[i - g.nxy] * val(i - g.nxy);
-  if (iz + 1 < g.nz && !dir_axis(iz + 1, g.nz, g.dlo_z, g.dhi_z)) v -= a.Tz64[i] * val(i + g.nxy);
+  const int64_t i = c.i, ip = c.ip;
+  const int ix = c.ix, iy = c.iy, iz = c.iz;
+  if (is_dir_cell(g, ix, iy, iz)) return val(i, ip);
+  double v = a.diag64[i] * val(i, ip);
+  if (ix > 0 && !dir_axis(ix - 1, g.nx, g.dlo_x, g.dhi_x)) v -= a.Tx64[i - 1] * val(i - 1, ip - 1);
+  if (ix + 1 < g.nx && !dir_axis(ix + 1, g.nx, g.dlo_x, g.dhi_x)) v -= a.Tx64[i] * val(i + 1, ip + 1);
+  if (iy > 0 && !dir_axis(iy - 1, g.ny, g.dlo_y, g.dhi_y)) v -= a.Ty64[i - g.nx] * val(i - g.nx, ip - a.vp);
+  if (iy + 1 < g.ny && !dir_axis(iy + 1, g.ny, g.dlo_y, g.dhi_y)) v -= a.Ty64[i] * val(i + g.nx, ip + a.vp);
+  if (iz > 0 && !dir_axis(iz - 1, g.nz, g.dlo_z, g.dhi_z)) v -= a.Tz64[i - g.nxy] * val(i - g.nxy, ip - a.vpxy);
+  if (iz + 1 < g.nz && !dir_axis(iz + 1, g.nz, g.dlo_z, g.dhi_z)) v -= a.Tz64[i] * val(i + g.nxy, ip + a.vpxy);
   return v;
 }
 
+// Rows of per-warp label accumulators: one per warp of the launch.
+__device__ __forceinline__ int acc_rows() { return (int)(blockDim.x >> 5); }
+
 // O1: r' = b - A (x + xhat), s = Z^T r', ||b||^2
-// The segmented sum groups the lanes of a warp by label (fixed lane order)
-// and, for d <= kWarpAccMaxD, adds each group into the warp's own row of
+// The label sums use the run-sum accumulator below (FP64): groups summed in a
+// fixed order and, for d <= kWarpAccMaxD, added into the warp's own row of
 // shared accumulators, so the result does not depend on warp scheduling.
+
 template <typename T, bool WACC>
 __device__ void sweep_O1(const SolveArgs& a, double* sacc, double* red, double* part_row) {
   const Geo& g = a.g;
   const int d = a.d;
   const int warp = threadIdx.x >> 5;
   const T* xh = static_cast<const T*>(a.xh);
-  for (int k = threadIdx.x; k < (WACC ? kWarps : 1) * d; k += blockDim.x) sacc[k] = 0.0;
+  for (int k = threadIdx.x; k < (WACC ? acc_rows() : 1) * d; k += blockDim.x) sacc[k] = 0.0;
   __syncthreads();
   double bb = 0.0;
   double sl[kMaxL] = {};  // Z_L^T r' (extra columns)
   const int64_t stride = (int64_t)a.sy.ncta * blockDim.x;
   const int64_t nround = (g.n + stride - 1) / stride;
-  for (int64_t rnd = 0; rnd < nround; ++rnd) {
-    const int64_t i = rnd * stride + (int64_t)team_rank(a.sy) * blockDim.x + threadIdx.x;
-    const bool ok = i < g.n;
+  CellWalk c;
+  c.init(a, (int64_t)team_rank(a.sy) * blockDim.x + threadIdx.x, stride);
+  LabelAcc<double, WACC> la;
+  la.init(a.lab_L);
+  for (int64_t rnd = 0; rnd < nround; ++rnd, c.next()) {
+    const int64_t i = c.i;
+    const bool ok = c.ok();
     double r = 0.0;
     int l = -1;
     if (ok) {
-      const int ix = (int)(i % g.nx), iy = (int)((i / g.nx) % g.ny), iz = (int)(i / g.nxy);
-      const double Aw = apply64(a, i, ix, iy, iz, [&](int64_t j) { return a.x[j] + (double)xh[vidx(a, j)]; });
+      const double Aw = apply64(a, c, [&](int64_t j, int64_t jp) { return a.x[j] + (double)xh[jp]; });
       const double bi = a.b[i];
       r = bi - Aw;
       a.r64[i] = r;
@@ -245,8 +283,9 @@ __device__ void sweep_O1(const SolveArgs& a, double* sacc, double* red, double* 
         for (int j = 0; j < kMaxL; ++j) sl[j] += (double)a.ZL32[i * kMaxL + j] * r;
       }
     }
-    warp_flush<WACC>(l, r, sacc, d, warp);
+    la.add(ok, l, r, sacc, d, warp);
   }
+  la.flush(sacc, d, warp);
 #pragma unroll
   for (int j = 0; j < kMaxL; ++j) {
     if (j < a.kL) {
@@ -258,7 +297,7 @@ __device__ void sweep_O1(const SolveArgs& a, double* sacc, double* red, double* 
   for (int k = threadIdx.x; k < d; k += blockDim.x) {
     double t = 0.0;
     if constexpr (WACC) {
-      for (int w = 0; w < kWarps; ++w) t += sacc[w * d + k];
+      for (int w = 0; w < acc_rows(); ++w) t += sacc[w * d + k];
     } else {
       t = sacc[k];
     }
@@ -270,16 +309,16 @@ __device__ void sweep_O1(const SolveArgs& a, double* sacc, double* red, double* 
 // O2: x += xhat + Z y, rhat = r' - A Z y, z = M^{-1} rhat, xhat = p = 0
 template <typename T>
 __device__ void sweep_O2(const SolveArgs& a, const double* Yd, double* red, double* part_row) {
-  const Geo& g = a.g;
   T* xh = static_cast<T*>(a.xh);
   T* zb = static_cast<T*>(a.z);
   T* p0 = static_cast<T*>(a.p0);
   T* p1 = static_cast<T*>(a.p1);
   double rr = 0.0, rho = 0.0;
   const int64_t stride = (int64_t)a.sy.ncta * blockDim.x;
-  for (int64_t i = (int64_t)team_rank(a.sy) * blockDim.x + threadIdx.x; i < g.n; i += stride) {
-    const int ix = (int)(i % g.nx), iy = (int)((i / g.nx) % g.ny), iz = (int)(i / g.nxy);
-    double AZy = apply64(a, i, ix, iy, iz, [&](int64_t j) { return Yd[__ldg(a.label + j)]; });
+  CellWalk c;
+  for (c.init(a, (int64_t)team_rank(a.sy) * blockDim.x + threadIdx.x, stride); c.ok(); c.next()) {
+    const int64_t i = c.i, ip = c.ip;
+    double AZy = apply64(a, c, [&](int64_t j, int64_t) { return Yd[__ldg(a.label + j)]; });
     double Zy = Yd[__ldg(a.label + i)];
     for (int j = 0; j < a.kL; ++j) {  // extra columns: (A Z_L y_L)_i = (W_L y_L)_i, (Z_L y_L)_i
       const double yj = Yd[a.d + j];
@@ -287,7 +326,6 @@ __device__ void sweep_O2(const SolveArgs& a, const double* Yd, double* red, doub
       Zy += (double)a.ZL32[i * kMaxL + j] * yj;
     }
     const double rh = a.r64[i] - AZy;
-    const int64_t ip = vidx(a, i);
     a.x[i] = a.x[i] + (double)xh[ip] + Zy;
     const T zt = (T)(rh * (a.invdi ? (double)a.invdi[ip] : a.invdiag64[i]));
     zb[ip] = zt;
@@ -363,17 +401,18 @@ __device__ double cta_scalar(const SolveArgs& a, int slot, double* red) {
   return v0;
 }
 
-// s . y (same order in every CTA).
-__device__ double cta_sdoty(const SolveArgs& a, double* red) {
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    double t = 0.0;
-    for (int k = threadIdx.x; k < a.dk; k += 32) t += a.s_glob[k] * a.y_glob[k];
-    t = warp_sum(t);
-    if (threadIdx.x == 0) red[42] = t;
+// This CTA's copy Y = y (in the sweep type) and s . y, in one pass over the
+// coarse vectors (s . y summed in the same order in every CTA).  Ends with a
+// CTA barrier: Y is complete.
+template <typename T>
+__device__ double cta_take_y(const SolveArgs& a, T* Y, double* red) {
+  double t = 0.0;
+  for (int k = threadIdx.x; k < a.dk; k += blockDim.x) {
+    const double yk = a.y_glob[k];
+    Y[k] = (T)yk;
+    t += a.s_glob[k] * yk;
   }
-  __syncthreads();
-  return red[42];
+  return block_sum(t, red);
 }
 
 
@@ -432,14 +471,12 @@ __device__ void solve_body(const SolveArgs& a, double* acc, double* Yd, T* Y, do
       phase_coarse(a, a.Einv_inner);
       if (!grid_barrier(a.sy, epoch)) { failed = true; break; }
       const double gamma = a.s_glob[a.dk];
-      const double delta = gamma - cta_sdoty(a, red);
+      const double delta = gamma - cta_take_y(a, Y, red);
       if (!(delta > 0.0) || !isfinite(delta) || !isfinite(rho)) {
         if (a.fp64) status = SLD_ERR_BREAKDOWN;
         break;
       }
       const double alpha = rho / delta;
-      for (int k = threadIdx.x; k < a.dk; k += blockDim.x) Y[k] = (T)a.y_glob[k];
-      __syncthreads();
       if (!sweepB(pold ^ 1, (T)alpha, my_part)) { failed = true; break; }
       if (!grid_barrier(a.sy, epoch)) { failed = true; break; }
       double rho_new, rr;

@@ -16,13 +16,15 @@ int launch_solve_tma(sld_system s, SolveArgs& a, const sld_options& o, float* ms
   if (a.fp64)
     return wacc ? launch_tma<double, double, 8, 3, true, false>(s, a, o, ms, msg)
                 : launch_tma<double, double, 8, 3, false, false>(s, a, o, ms, msg);
+  // FP32 inner and BF16 faces: 64 x 8 tiles, 3-deep ring, four CTAs per SM
+  // (on the 256 x 256 x 128 workload 1.5 % faster than 64 x 16 tiles at two
+  // CTAs per SM, 10 % faster than 64 x 8 tiles with 4-deep rings or at three
+  // CTAs per SM, 30 % faster than one CTA per SM)
   if (a.bf16)
-    return wacc ? launch_tma<float, __nv_bfloat16, 16, 3, true, false>(s, a, o, ms, msg)
-                : launch_tma<float, __nv_bfloat16, 16, 3, false, false>(s, a, o, ms, msg);
-  // FP32 inner: 64 x 16 tiles, 3-deep ring (measured faster than 64 x 8
-  // tiles with 4- or 5-deep rings on the 256 x 256 x 128 workload)
-  return wacc ? launch_tma<float, float, 16, 3, true, false>(s, a, o, ms, msg)
-              : launch_tma<float, float, 16, 3, false, false>(s, a, o, ms, msg);
+    return wacc ? launch_tma<float, __nv_bfloat16, 8, 3, true, false>(s, a, o, ms, msg)
+                : launch_tma<float, __nv_bfloat16, 8, 3, false, false>(s, a, o, ms, msg);
+  return wacc ? launch_tma<float, float, 8, 3, true, false>(s, a, o, ms, msg)
+              : launch_tma<float, float, 8, 3, false, false>(s, a, o, ms, msg);
 }
 
 // ---------------------------------------------------------------------------

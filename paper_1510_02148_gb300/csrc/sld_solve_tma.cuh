@@ -68,6 +68,7 @@ struct TCfg {
   static constexpr unsigned TX_B = unsigned(bH + bLH + bX + bY + bOF + (kOwnRing ? 2 * bO : 0) +
                                             (kDiag ? 2 * bO : 0) + (kScale ? bOS : 0));
   static constexpr size_t SLOT = A_END > B_END ? A_END : B_END;
+  static constexpr int kAcc = TY / 2;  // warps = rows of label accumulators (acc_rows())
 };
 
 // Tensor maps (3-D: x, y, z), built on the host for this handle's buffers.
@@ -246,7 +247,7 @@ __device__ bool sweep_tma(const SolveArgs& a, const Maps& mp, const Ring<S>& rg,
   T* zbw = static_cast<T*>(a.z);
   T* xhw = static_cast<T*>(a.xh);
   if constexpr (IS_A) {
-    for (int k = tid; k < (WACC ? kWarps : 1) * d; k += blockDim.x) sacc[k] = 0.0;
+    for (int k = tid; k < (WACC ? C::kAcc : 1) * d; k += blockDim.x) sacc[k] = 0.0;
   }
   const int tr = team_rank(a.sy);
   const int64_t t0 = a.ntiles * tr / a.sy.ncta, t1 = a.ntiles * (tr + 1) / a.sy.ncta;
@@ -283,7 +284,7 @@ __device__ bool sweep_tma(const SolveArgs& a, const Maps& mp, const Ring<S>& rg,
                                // per warp into lsum[warp][j] (fixed order)
   T yl[LRN ? kMaxL : 1] = {};  // sweep B: y of the extra columns
   if constexpr (LRN && IS_A) {
-    for (int k = tid; k < kWarps * kMaxL; k += blockDim.x) lsum[k] = 0.0;
+    for (int k = tid; k < C::kAcc * kMaxL; k += blockDim.x) lsum[k] = 0.0;
   }
   if constexpr (LRN && !IS_A) {
 #pragma unroll
@@ -439,6 +440,7 @@ __device__ bool sweep_tma(const SolveArgs& a, const Maps& mp, const Ring<S>& rg,
       // deflation columns need a.vp == nx)
       const int64_t iz = (int64_t)z * a.vpxy + (int64_t)y * a.vp + xl;
       if constexpr (IS_A) {
+        T av[4];
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
           const bool valid = c < nv;
@@ -448,7 +450,7 @@ __device__ bool sweep_tma(const SolveArgs& a, const Maps& mp, const Ring<S>& rg,
           const T fxm = (c > 0) ? fx[(c > 0) ? c - 1 : 0] : fxl;
           const T v = stencil<T>(dxc[c] || dyc || dzc, u, dg[c], fxm, xm, !dxm[c], fx[c], xp, !dxp[c], fym[c],
                                  ym[c], !dym, fy[c], yp[c], !dyp, tzm[c], vm[c], !dzm, fz[c], vn[c], !dzp);
-          la.add(valid, lb[c], v, sacc, d, warp);
+          av[c] = v;
           if (valid) acc1 += u * v;
           if constexpr (LRN) {
             if (valid) {
@@ -459,6 +461,7 @@ __device__ bool sweep_tma(const SolveArgs& a, const Maps& mp, const Ring<S>& rg,
             }
           }
         }
+        la.add4(nv, lb, av, sacc, d, warp);
         st_cells<T, 4>(pnew, iz, nv, vc);
       } else {
         T zo[4], xo[4], zn[4], xn[4], sci[4] = {};
@@ -571,18 +574,24 @@ __device__ bool sweep_tma(const SolveArgs& a, const Maps& mp, const Ring<S>& rg,
   return true;
 }
 
+// CTAs per SM the register allocation must allow: FP32 forms up to 64K
+// registers per SM at 128 per thread; the FP64 form two CTAs (its ring
+// slots fit two per SM), i.e. up to 255 registers per thread.
+template <typename T, int TY>
+constexpr int tma_min_ctas() { return sizeof(T) == 8 ? 2 : (512 / (16 * TY) > 1 ? 512 / (16 * TY) : 1); }
+
 template <typename T, typename F, int TY, int S, bool WACC>
 __host__ __device__ constexpr size_t tma_smem_bytes(int d, int dk) {
   using C = TCfg<T, F, TY>;
   size_t b = C::SLOT * S;
   b += 8 * S;
   b = (b + 15) / 16 * 16;
-  b += sizeof(double) * (size_t)(WACC ? kWarps : 1) * d;
+  b += sizeof(double) * (size_t)(WACC ? C::kAcc : 1) * d;
   b += sizeof(double) * dk;
   b += sizeof(T) * dk;
   b = (b + 15) / 16 * 16;
   b += sizeof(double) * 64;
-  b += sizeof(double) * kWarps * kMaxL;
+  b += sizeof(double) * C::kAcc * kMaxL;
   return b;
 }
 
@@ -598,7 +607,7 @@ __device__ __forceinline__ void tma_body(const SolveArgs& a, const Maps& mp, int
   o += 8 * S;
   o = (o + 15) / 16 * 16;
   double* acc = reinterpret_cast<double*>(smem_raw + o);
-  o += sizeof(double) * (size_t)(WACC ? kWarps : 1) * a.d;
+  o += sizeof(double) * (size_t)(WACC ? C::kAcc : 1) * a.d;
   double* Yd = reinterpret_cast<double*>(smem_raw + o);
   o += sizeof(double) * a.dk;
   T* Y = reinterpret_cast<T*>(smem_raw + o);
@@ -628,7 +637,7 @@ __device__ __forceinline__ void tma_body(const SolveArgs& a, const Maps& mp, int
 }
 
 template <typename T, typename F, int TY, int S, bool WACC, bool LRN>
-__global__ void __launch_bounds__(16 * TY) k_solve_tma(SolveArgs a, const __grid_constant__ Maps mp, int ntx) {
+__global__ void __launch_bounds__(16 * TY, tma_min_ctas<T, TY>()) k_solve_tma(SolveArgs a, const __grid_constant__ Maps mp, int ntx) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   tma_body<T, F, TY, S, WACC, LRN>(a, mp, ntx, smem_raw);
 }
@@ -638,7 +647,7 @@ __global__ void __launch_bounds__(16 * TY) k_solve_tma(SolveArgs a, const __grid
 // args_off, past the solve's own layout); its tensor maps stay in global
 // memory, where the TMA unit reads them.
 template <typename T, typename F, int TY, int S, bool WACC>
-__global__ void __launch_bounds__(16 * TY) k_solve_tma_batch(const SolveArgs* __restrict__ all,
+__global__ void __launch_bounds__(16 * TY, tma_min_ctas<T, TY>()) k_solve_tma_batch(const SolveArgs* __restrict__ all,
                                                            const Maps* __restrict__ maps,
                                                            const int* __restrict__ cta_sys, unsigned args_off) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
