@@ -701,7 +701,7 @@ sld_status sld_batch_create(sld_system* systems, int count, const sld_options* o
   }
   const sld::BatchPlan& p = bt->plan;
   bt->desc = "systems " + std::to_string(count) + ", CTAs " + std::to_string(p.G) + " (" + std::to_string(p.per_sm) +
-             " per SM), " + (p.tma ? std::string("TMA sweeps, 64x16 tiles") : "cells per lane " + std::to_string(p.cx)) +
+             " per SM), " + (p.tma ? std::string("TMA sweeps, 64x8 tiles") : "cells per lane " + std::to_string(p.cx)) +
              ", teams by " + (p.expo < 0 ? std::string("measured work") : "n^" + std::to_string(p.expo).substr(0, 4)) +
              ":";
   for (int k = 0; k < count; ++k) bt->desc += " " + std::to_string(p.teams[k]);
