@@ -163,6 +163,12 @@ __device__ __forceinline__ void fence_mbar_init() {
 // async-proxy (TMA) accesses, in global and shared memory.
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async;" ::: "memory"); }
 
+// Orders this thread's generic shared-memory accesses before later
+// async-proxy (TMA) accesses of the CTA's shared memory.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                : "memory");
