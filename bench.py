@@ -108,10 +108,8 @@ class ClockSampler:
 
 
 def _dist():
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return world, rank, local
+    from paper_1510_02148_gb300 import replicas
+    return replicas.dist_env()
 
 
 def cpu_baseline(P, A=None, lab=None, iters_full=None, sample_iters=40, threads=None):
@@ -304,18 +302,15 @@ def main():
         return profile_solve(args)
 
     import torch
-    from paper_1510_02148_gb300 import _build, sld, workloads as W
+    from paper_1510_02148_gb300 import _build, replicas, sld, workloads as W
 
-    world, rank, local = _dist()
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    world, rank, local = replicas.init(cuda=True)
     torch.cuda.set_device(local)
     _build.build()
     sld.load()
     stream = torch.cuda.current_stream()
 
-    P = W.lognormal_point_source(seed=1 + rank)
+    P = W.lognormal_point_source(seed=replicas.replica_seed(rank))
     Kd = torch.from_numpy(P.K.reshape(-1)).cuda()
     qd = torch.from_numpy(P.q.reshape(-1)).cuda()
     t0 = time.perf_counter()
@@ -327,10 +322,7 @@ def main():
     x = torch.empty(P.n, dtype=torch.float64, device="cuda")
 
     def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
-        torch.cuda.synchronize()
+        replicas.barrier(cuda=True)
 
     # --- plain FP64 (comparison) ---
     fp64 = []
@@ -352,12 +344,7 @@ def main():
         ev1.record(stream)
         barrier()
     total_ms = ev0.elapsed_time(ev1)
-    ms_step = total_ms / args.steps
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = replicas.max_over_ranks(total_ms / args.steps, cuda=True)
     info = infos[-1]
     kern_ms = statistics.median(i.solve_ms for i in infos)
     n = P.n
@@ -414,9 +401,7 @@ def main():
     s.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
-    if world > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
+    replicas.finish()
     return 0
 
 
