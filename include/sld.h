@@ -185,6 +185,40 @@ sld_status sld_deflation_info(sld_system s, int* d, int* k_requested, int* k_use
 sld_status sld_solve(sld_system s, const double* b, const sld_options* o, double* x,
                      sld_result* res);
 
+/*
+ * PDGMRES: restarted GMRES(m), right-preconditioned with Jacobi (M = diag A),
+ * deflated with the system's label columns Z (Section 3.2, the deflated
+ * GMRES of the paper with the physics-based vectors of Section 3.2.2 fixed
+ * before the iteration; its remark on right preconditioning: the deflation
+ * operators use A, not A M^{-1}):
+ *   E = Z^T A Z, P1 = I - A Z E^{-1} Z^T, P2 = I - Z E^{-1} Z^T A,
+ *   x* = Z E^{-1} Z^T b,  GMRES(m) on P1 A M^{-1} u = P1 b,
+ *   x = P2 M^{-1} u + x*   (b - A x = P1 (b - A M^{-1} u): the GMRES
+ *   residual is the residual of x).
+ * FP64 throughout; Arnoldi by classical Gram-Schmidt with one
+ * reorthogonalisation; the Givens least-squares problem on the host.  Each
+ * cycle starts from the recomputed residual; a cycle ends after m steps, or
+ * when ||b - A x|| <= tol ||b|| by the Givens estimate, or at maxiter steps.
+ *   b: n values (host or device), or NULL for the assembled rhs.
+ *   m: 1 .. 31 (cycle length).  deflate: 1 = use the label columns (needs
+ *   sld_build_deflation, label columns only), 0 = plain GMRES(m).
+ *   tol: in (0, 1).  maxiter >= 1: Arnoldi steps over all cycles.
+ *   x: n values (output, host or device).  info: may be NULL.
+ * Work space: (m + 4) n FP64 on the device, allocated per call.
+ * Errors: SLD_ERR_INVALID_ARG, SLD_ERR_STATE, SLD_ERR_OOM, SLD_ERR_CUDA,
+ * SLD_ERR_NOT_CONVERGED (x and info still written).
+ */
+typedef struct {
+  int iterations;          /* Arnoldi steps over all cycles */
+  int cycles;              /* restart cycles */
+  double relres_estimate;  /* ||b - A x|| / ||b|| from the Givens recurrence at exit */
+  double true_relres;      /* ||b - A x|| / ||b||, recomputed in FP64 from x */
+  double solve_ms;         /* device time of the whole solve (CUDA events) */
+} sld_gmres_info;
+
+sld_status sld_solve_gmres(sld_system s, const double* b, int m, int deflate, double tol, int maxiter,
+                           double* x, sld_gmres_info* info);
+
 /* Release the handle and its device memory.  NULL is ignored. */
 void sld_destroy(sld_system s);
 

@@ -1,0 +1,434 @@
+// sld_gmres.cu -- PDGMRES: restarted GMRES(m), right-preconditioned with
+// Jacobi, deflated with the subdomain-levelset columns (Section 3.2, with the
+// physics-based vectors of Section 3.2.2 built before the iteration):
+//
+//   E = Z^T A Z,  P1 = I - A Z E^{-1} Z^T,  P2 = I - Z E^{-1} Z^T A,
+//   x* = Z E^{-1} Z^T b;  GMRES(m) on P1 A M^{-1} u = P1 b,  M = diag A;
+//   x = P2 x~ + x*,  x~ = M^{-1} u   (b - A x = P1 (b - A x~)).
+//
+// One Arnoldi step, FP64, stream-ordered kernels over all cells:
+//   k_gm_apply     w = A M^{-1} v_j, v_j = raw / |raw| written to the basis,
+//                  and this CTA's Z^T w (fixed-order label sums)
+//   k_gm_colsum    s = the column sums of those rows;  k_gm_gemv  y = E^{-1} s
+//   k_gm_defl      w -= A Z y   (the 7-point stencil on y[label])
+//   k_gm_dots      h1 = V^T w   (8 basis vectors per CTA row of the grid)
+//   k_gm_orth      w -= V h1
+//   k_gm_dots      h2 = V^T w
+//   k_gm_orth      raw = w - V h2, |raw|^2
+// Classical Gram-Schmidt with one reorthogonalisation (two passes over the
+// basis, each fully parallel) stands in for the sequential modified
+// Gram-Schmidt; the Hessenberg column is h1 + h2 and h_{j+1,j} = |raw|.  One
+// device-to-host copy per step brings it to the host, which applies the
+// Givens rotations, tests the residual estimate and, at the end of a cycle,
+// solves the small triangular system.  Every sum is a per-CTA partial row
+// reduced in a fixed order.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "sld_solve_common.cuh"
+
+namespace sld {
+namespace {
+
+constexpr int kGT = 256;         // threads per CTA
+constexpr int kGMaxBasis = 32;   // basis vectors (m + 1)
+constexpr int kGDots = 8;        // basis vectors per CTA in k_gm_dots
+
+enum { GM_PRECOND = 0, GM_RESID = 1, GM_APPLY = 2, GM_COPY = 3 };
+
+// w = op(v) at every cell, and this CTA's row of Z^T w.
+//   GM_PRECOND: v is the raw next basis vector; v_j = v / sqrt(*norm2) is
+//               written to vout and w = A M^{-1} v_j
+//   GM_RESID:   w = b - A v        GM_APPLY: w = A v        GM_COPY: w = v (not stored)
+template <int MODE, bool WACC>
+__global__ void __launch_bounds__(kGT) k_gm_apply(SolveArgs a, const double* __restrict__ v,
+                                                  const double* __restrict__ norm2, double* __restrict__ vout,
+                                                  double* __restrict__ w, double* __restrict__ part) {
+  extern __shared__ double sacc[];
+  const int d = a.d;
+  const int warp = threadIdx.x >> 5;
+  for (int k = threadIdx.x; k < (WACC ? acc_rows() : 1) * d; k += blockDim.x) sacc[k] = 0.0;
+  __syncthreads();
+  double sc = 1.0;
+  if constexpr (MODE == GM_PRECOND) sc = 1.0 / sqrt(*norm2);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t nround = (a.g.n + stride - 1) / stride;
+  CellWalk c;
+  c.init(a, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, stride);
+  LabelAcc<double, WACC> la;
+  la.init(a.lab_L);
+  for (int64_t rnd = 0; rnd < nround; ++rnd, c.next()) {
+    const bool ok = c.ok();
+    double wv = 0.0;
+    int l = -1;
+    if (ok) {
+      const int64_t i = c.i;
+      if constexpr (MODE == GM_PRECOND) {
+        wv = apply64(a, c, [&](int64_t j, int64_t) { return (v[j] * sc) * a.invdiag64[j]; });
+        vout[i] = v[i] * sc;
+      } else if constexpr (MODE == GM_RESID) {
+        wv = a.b[i] - apply64(a, c, [&](int64_t j, int64_t) { return v[j]; });
+      } else if constexpr (MODE == GM_APPLY) {
+        wv = apply64(a, c, [&](int64_t j, int64_t) { return v[j]; });
+      } else {
+        wv = v[i];
+      }
+      if constexpr (MODE != GM_COPY) w[i] = wv;
+      if (d > 0) l = a.label[i];
+    }
+    if (d > 0) la.add(ok, l, wv, sacc, d, warp);
+  }
+  if (d > 0) {
+    la.flush(sacc, d, warp);
+    __syncthreads();
+    for (int k = threadIdx.x; k < d; k += blockDim.x) {
+      double t = 0.0;
+      if constexpr (WACC) {
+        for (int r = 0; r < acc_rows(); ++r) t += sacc[r * d + k];
+      } else {
+        t = sacc[k];
+      }
+      part[(int64_t)k * a.pstride + blockIdx.x] = t;
+    }
+  }
+}
+
+// out[k] = sum of column k of the partial rows (G CTAs), k < ncol; one warp
+// per column, the same order every time.
+__global__ void k_gm_colsum(const double* __restrict__ part, int pstride, int G, int ncol, double* __restrict__ out) {
+  const int col = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (col >= ncol) return;
+  const double* p = part + (int64_t)col * pstride;
+  double t = 0.0;
+  for (int c = lane; c < G; c += 32) t += p[c];
+  t = warp_sum(t);
+  if (lane == 0) out[col] = t;
+}
+
+// y = E^{-1} s, one warp per row.
+__global__ void k_gm_gemv(int d, const double* __restrict__ Einv, const double* __restrict__ s, double* __restrict__ y) {
+  const int row = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (row >= d) return;
+  double t = 0.0;
+  for (int k = lane; k < d; k += 32) t += Einv[(int64_t)row * d + k] * s[k];
+  t = warp_sum(t);
+  if (lane == 0) y[row] = t;
+}
+
+// w -= A Z y  ((A Z y)_i: the stencil applied to the cellwise y[label]).
+__global__ void __launch_bounds__(kGT) k_gm_defl(SolveArgs a, const double* __restrict__ y, double* __restrict__ w) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  CellWalk c;
+  for (c.init(a, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, stride); c.ok(); c.next())
+    w[c.i] -= apply64(a, c, [&](int64_t j, int64_t) { return y[__ldg(a.label + j)]; });
+}
+
+// Partial rows of V_k . w for the kGDots basis vectors k0 = blockIdx.y * kGDots ..
+__global__ void __launch_bounds__(kGT) k_gm_dots(int64_t n, const double* __restrict__ V, int nv,
+                                                 const double* __restrict__ w, double* __restrict__ part,
+                                                 int pstride) {
+  __shared__ double red[kGDots][kGT / 32];
+  const int k0 = blockIdx.y * kGDots;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double acc[kGDots];
+#pragma unroll
+  for (int k = 0; k < kGDots; ++k) acc[k] = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double wi = w[i];
+#pragma unroll
+    for (int k = 0; k < kGDots; ++k)
+      if (k0 + k < nv) acc[k] += V[(int64_t)(k0 + k) * n + i] * wi;
+  }
+#pragma unroll
+  for (int k = 0; k < kGDots; ++k) {
+    const double t = warp_sum(acc[k]);
+    if (lane == 0) red[k][warp] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x < kGDots && k0 + (int)threadIdx.x < nv) {
+    double t = 0.0;
+    for (int q = 0; q < kGT / 32; ++q) t += red[threadIdx.x][q];
+    part[(int64_t)(k0 + threadIdx.x) * pstride + blockIdx.x] = t;
+  }
+}
+
+// out = w - sum_{k < nv} h[k] V_k (out may be w); with norm_col >= 0 also the
+// partial row of |out|^2 in that column.
+__global__ void __launch_bounds__(kGT) k_gm_orth(int64_t n, const double* __restrict__ V, int nv,
+                                                 const double* __restrict__ h, const double* w, double* out,
+                                                 double* __restrict__ part, int pstride, int norm_col) {
+  __shared__ double hs[kGMaxBasis];
+  __shared__ double red[kGT / 32];
+  if (threadIdx.x < kGMaxBasis) hs[threadIdx.x] = (int)threadIdx.x < nv ? h[threadIdx.x] : 0.0;
+  __syncthreads();
+  double nn = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double t = w[i];
+    for (int k = 0; k < nv; ++k) t -= hs[k] * V[(int64_t)k * n + i];
+    out[i] = t;
+    nn += t * t;
+  }
+  if (norm_col < 0) return;
+  nn = warp_sum(nn);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = nn;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < kGT / 32; ++q) t += red[q];
+    part[(int64_t)norm_col * pstride + blockIdx.x] = t;
+  }
+}
+
+// x~ += M^{-1} sum_{k < nv} u[k] V_k
+__global__ void __launch_bounds__(kGT) k_gm_update(int64_t n, const double* __restrict__ V, int nv,
+                                                   const double* __restrict__ u, const double* __restrict__ invdiag,
+                                                   double* __restrict__ xt) {
+  __shared__ double us[kGMaxBasis];
+  if (threadIdx.x < kGMaxBasis) us[threadIdx.x] = (int)threadIdx.x < nv ? u[threadIdx.x] : 0.0;
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double t = 0.0;
+    for (int k = 0; k < nv; ++k) t += us[k] * V[(int64_t)k * n + i];
+    xt[i] += invdiag[i] * t;
+  }
+}
+
+// x = x~ - Z y1 + Z y0   (P2 x~ + x*, y1 = E^{-1} Z^T A x~, y0 = E^{-1} Z^T b)
+__global__ void k_gm_final(int64_t n, const int32_t* __restrict__ label, const double* __restrict__ xt,
+                           const double* __restrict__ y1, const double* __restrict__ y0, double* __restrict__ x) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const int l = label[i];
+    x[i] = xt[i] - y1[l] + y0[l];
+  }
+}
+
+// Device scalars of the solve (one block, copied to the host once per step).
+struct Scal {
+  double h1[kGMaxBasis];
+  double h2[kGMaxBasis];
+  double nn;  // |raw|^2 of the vector the next step normalises
+  double pad[7];
+};
+
+}  // namespace
+
+int run_gmres(sld_system s, const double* b, int m, int deflate, double tol, int maxiter, sld_gmres_info* info,
+              std::string* msg) {
+  const int64_t n = s->g.n;
+  cudaStream_t st = s->stream;
+  sld_options o;
+  sld_default_options(&o);
+  o.precision = SLD_FP64;
+  SolveArgs a;
+  fill_args(s, b, o, &a);
+  const int d = deflate ? s->d : 0;
+  a.d = d;
+  a.dk = d;
+  a.kL = 0;
+  const bool wacc = d <= kWarpAccMaxD;
+  const int G = std::min(s->nsm * 4, s->part_rows);
+  a.sy.ncta = G;
+  a.sy.cta0 = 0;
+  const int ps = a.pstride;
+  double* part = a.part;
+  // work space: the basis (m + 1) n, w, raw, x~ (n each), small vectors
+  double* V = nullptr;
+  double* work = nullptr;
+  Scal* sc = nullptr;
+  const size_t small = (size_t)4 * (d + 1) + kGMaxBasis;
+  auto release = [&]() {
+    cudaFree(V);
+    cudaFree(work);
+    cudaFree(sc);
+  };
+  cudaError_t e = cudaMalloc(&V, sizeof(double) * (size_t)(m + 1) * n);
+  if (e == cudaSuccess) e = cudaMalloc(&work, sizeof(double) * ((size_t)3 * n + small));
+  if (e == cudaSuccess) e = cudaMalloc(&sc, sizeof(Scal));
+  if (e != cudaSuccess) {
+    release();
+    *msg = std::string("GMRES work space: ") + cudaGetErrorString(e);
+    return SLD_ERR_OOM;
+  }
+  double *w = work, *raw = w + n, *xt = raw + n;
+  double *sv = xt + n, *y = sv + (d + 1), *y0 = y + (d + 1), *y1 = y0 + (d + 1), *ud = y1 + (d + 1);
+  const size_t smem = sizeof(double) * (size_t)(wacc ? kGT / 32 : 1) * (size_t)std::max(d, 1);
+  // colsum / gemv: one warp per column (row), 8 warps per block
+  auto cols = [&](int ncol) { return dim3((unsigned)((ncol + 7) / 8)); };
+  auto colsum = [&](int ncol, double* out) {
+    k_gm_colsum<<<cols(ncol), 256, 0, st>>>(part, ps, G, ncol, out);
+  };
+  // s = Z^T (partials from the last k_gm_apply), y = E^{-1} s
+  auto coarse = [&](double* yout) {
+    colsum(d, sv);
+    k_gm_gemv<<<cols(d), 256, 0, st>>>(d, a.Einv, sv, yout);
+  };
+  auto apply = [&](int mode, const double* v, const double* nrm2, double* vout, double* wout) {
+#define GM_LAUNCH(MODE)                                                                              \
+  (wacc ? k_gm_apply<MODE, true><<<G, kGT, smem, st>>>(a, v, nrm2, vout, wout, part)                  \
+        : k_gm_apply<MODE, false><<<G, kGT, smem, st>>>(a, v, nrm2, vout, wout, part))
+    switch (mode) {
+      case GM_PRECOND: GM_LAUNCH(GM_PRECOND); break;
+      case GM_RESID: GM_LAUNCH(GM_RESID); break;
+      case GM_APPLY: GM_LAUNCH(GM_APPLY); break;
+      default: GM_LAUNCH(GM_COPY); break;
+    }
+#undef GM_LAUNCH
+  };
+  auto dots = [&](int nv, double* out) {
+    k_gm_dots<<<dim3(G, (nv + kGDots - 1) / kGDots), kGT, 0, st>>>(n, V, nv, w, part, ps);
+    colsum(nv, out);
+  };
+  std::vector<double> H((size_t)(m + 1) * m), R((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), u(m);
+  cudaEventRecord(s->ev0, st);
+  // ||b||, and x* = Z y0 with y0 = E^{-1} Z^T b
+  k_gm_orth<<<G, kGT, 0, st>>>(n, V, 0, sc->h1, b, raw, part, ps, 0);
+  colsum(1, &sc->nn);
+  double bb = 0.0;
+  if ((e = cudaMemcpyAsync(&bb, &sc->nn, sizeof(double), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(st)) != cudaSuccess) {
+    release();
+    *msg = std::string("GMRES: ") + cudaGetErrorString(e);
+    return SLD_ERR_CUDA;
+  }
+  const double bnorm = std::sqrt(bb);
+  if (d > 0) {
+    apply(GM_COPY, b, nullptr, nullptr, nullptr);
+    coarse(y0);
+  }
+  cudaMemsetAsync(xt, 0, sizeof(double) * n, st);
+  int its = 0, cycles = 0;
+  bool converged = bnorm == 0.0;
+  double est = 0.0;
+  Scal hs;
+  auto fetch = [&]() -> bool {
+    if ((e = cudaMemcpyAsync(&hs, sc, sizeof(Scal), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return false;
+    return (e = cudaStreamSynchronize(st)) == cudaSuccess;
+  };
+  while (!converged) {
+    // r = P1 (b - A x~): raw, |raw|^2
+    apply(GM_RESID, xt, nullptr, nullptr, w);
+    if (d > 0) {
+      coarse(y);
+      k_gm_defl<<<G, kGT, 0, st>>>(a, y, w);
+    }
+    k_gm_orth<<<G, kGT, 0, st>>>(n, V, 0, sc->h1, w, raw, part, ps, 0);
+    colsum(1, &sc->nn);
+    if (!fetch()) break;
+    const double beta = std::sqrt(hs.nn);
+    est = bnorm > 0 ? beta / bnorm : 0.0;
+    if (beta <= tol * bnorm) {
+      converged = true;
+      break;
+    }
+    if (its >= maxiter) break;
+    ++cycles;
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int k = 0;
+    for (int j = 0; j < m; ++j) {
+      // v_j = raw / |raw|, w = P1 A M^{-1} v_j
+      apply(GM_PRECOND, raw, &sc->nn, V + (size_t)j * n, w);
+      if (d > 0) {
+        coarse(y);
+        k_gm_defl<<<G, kGT, 0, st>>>(a, y, w);
+      }
+      // classical Gram-Schmidt, twice
+      dots(j + 1, sc->h1);
+      k_gm_orth<<<G, kGT, 0, st>>>(n, V, j + 1, sc->h1, w, w, part, ps, -1);
+      dots(j + 1, sc->h2);
+      k_gm_orth<<<G, kGT, 0, st>>>(n, V, j + 1, sc->h2, w, raw, part, ps, 0);
+      colsum(1, &sc->nn);
+      if (!fetch()) break;
+      // Hessenberg column j, the earlier rotations, a new one for row j+1
+      std::vector<double> col(j + 2);
+      for (int i = 0; i <= j; ++i) col[i] = H[(size_t)i * m + j] = hs.h1[i] + hs.h2[i];
+      const double hn = std::sqrt(hs.nn);
+      col[j + 1] = H[(size_t)(j + 1) * m + j] = hn;
+      for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * col[i] + sn[i] * col[i + 1];
+        col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+        col[i] = t;
+      }
+      const double rho = std::hypot(col[j], col[j + 1]);
+      if (rho == 0.0) {
+        cs[j] = 1.0;
+        sn[j] = 0.0;
+      } else {
+        cs[j] = col[j] / rho;
+        sn[j] = col[j + 1] / rho;
+      }
+      col[j] = rho;
+      col[j + 1] = 0.0;
+      for (int i = 0; i <= j + 1; ++i) R[(size_t)i * m + j] = col[i];
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      ++its;
+      k = j + 1;
+      est = std::fabs(g[j + 1]) / bnorm;
+      if (std::fabs(g[j + 1]) <= tol * bnorm || hn == 0.0 || its >= maxiter) break;
+    }
+    if (e != cudaSuccess) break;
+    // R u = g (upper triangular, k x k), then x~ += M^{-1} V u
+    for (int i = k - 1; i >= 0; --i) {
+      double t = g[i];
+      for (int q = i + 1; q < k; ++q) t -= R[(size_t)i * m + q] * u[q];
+      u[i] = R[(size_t)i * m + i] != 0.0 ? t / R[(size_t)i * m + i] : 0.0;
+    }
+    if (k > 0) {
+      cudaMemcpyAsync(ud, u.data(), sizeof(double) * k, cudaMemcpyHostToDevice, st);
+      k_gm_update<<<G, kGT, 0, st>>>(n, V, k, ud, a.invdiag64, xt);
+    }
+    if (its >= maxiter) {
+      // one more residual evaluation decides convergence at the cap
+      apply(GM_RESID, xt, nullptr, nullptr, w);
+      if (d > 0) {
+        coarse(y);
+        k_gm_defl<<<G, kGT, 0, st>>>(a, y, w);
+      }
+      k_gm_orth<<<G, kGT, 0, st>>>(n, V, 0, sc->h1, w, raw, part, ps, 0);
+      colsum(1, &sc->nn);
+      if (!fetch()) break;
+      est = bnorm > 0 ? std::sqrt(hs.nn) / bnorm : 0.0;
+      converged = std::sqrt(hs.nn) <= tol * bnorm;
+      break;
+    }
+  }
+  if (e != cudaSuccess) {
+    release();
+    *msg = std::string("GMRES: ") + cudaGetErrorString(e);
+    return SLD_ERR_CUDA;
+  }
+  // x = P2 x~ + x*
+  if (d > 0) {
+    apply(GM_APPLY, xt, nullptr, nullptr, w);
+    coarse(y1);
+    k_gm_final<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, a.label, xt, y1, y0, a.x);
+  } else {
+    cudaMemcpyAsync(a.x, xt, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
+  }
+  cudaEventRecord(s->ev1, st);
+  e = cudaEventSynchronize(s->ev1);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  float ms = 0.0f;
+  cudaEventElapsedTime(&ms, s->ev0, s->ev1);
+  release();
+  if (e != cudaSuccess) {
+    *msg = std::string("GMRES: ") + cudaGetErrorString(e);
+    return SLD_ERR_CUDA;
+  }
+  info->iterations = its;
+  info->cycles = cycles;
+  info->relres_estimate = est;
+  info->solve_ms = ms;
+  if (!converged) {
+    *msg = "GMRES did not reach the tolerance within maxiter steps";
+    return SLD_ERR_NOT_CONVERGED;
+  }
+  return SLD_OK;
+}
+
+}  // namespace sld

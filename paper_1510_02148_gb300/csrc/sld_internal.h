@@ -167,6 +167,10 @@ cudaError_t tma_batch_launch(int G, size_t smem, unsigned args_off, bool wacc, c
 int launch_solve_tma_learned(sld_system s, SolveArgs& a, const sld_options& o, float* ms, std::string* msg);
 // sld_api.cu: the thread-local message returned by sld_last_error()
 void set_last_error(const std::string& msg);
+// sld_gmres.cu: PDGMRES (deflated right-Jacobi restarted GMRES, FP64);
+// b: device.  Writes the solution to s->x.  Returns an sld_status.
+int run_gmres(sld_system s, const double* b, int m, int deflate, double tol, int maxiter, sld_gmres_info* info,
+              std::string* msg);
 // sld_solve.cu
 void fill_args(sld_system s, const double* b_dev, const sld_options& o, SolveArgs* a);
 int run_solve(sld_system s, const double* b_dev, const sld_options& o, sld_result* res,

@@ -33,7 +33,7 @@ EXPORTED = ["sld_default_options", "sld_build_system", "sld_make_labels", "sld_b
             "sld_batch_describe", "sld_batch_destroy", "sld_solve_batched", "sld_deflation_info",
             "sld_net_num_params", "sld_net_create", "sld_net_set_params", "sld_net_get_params",
             "sld_net_get_grads", "sld_net_forward", "sld_net_backward", "sld_net_loss_backward",
-            "sld_net_adam", "sld_net_destroy", "sld_lanczos_eigvecs"]
+            "sld_net_adam", "sld_net_destroy", "sld_lanczos_eigvecs", "sld_solve_gmres"]
 
 
 class SldError(RuntimeError):
@@ -59,6 +59,11 @@ class Options(C.Structure):
 class Result(C.Structure):
     _fields_ = [("iterations", C.c_int), ("outer_steps", C.c_int), ("true_relres", C.c_double),
                 ("recursive_relres", C.c_double), ("solve_ms", C.c_double), ("kernel_path", C.c_int)]
+
+
+class GmresInfo(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("cycles", C.c_int), ("relres_estimate", C.c_double),
+                ("true_relres", C.c_double), ("solve_ms", C.c_double)]
 
 
 _lib = None
@@ -109,6 +114,7 @@ def load(path: str = LIB_PATH):
         lib.sld_net_destroy.argtypes = [P]
         lib.sld_net_destroy.restype = None
         lib.sld_lanczos_eigvecs.argtypes = [P, C.c_int, C.c_int, P, P, P]
+        lib.sld_solve_gmres.argtypes = [P, P, C.c_int, C.c_int, C.c_double, C.c_int, P, C.POINTER(GmresInfo)]
         for name in ("sld_build_system", "sld_make_labels", "sld_build_deflation", "sld_solve",
                      "sld_get_operator", "sld_apply_A", "sld_restrict", "sld_get_coarse",
                      "sld_batch_create", "sld_batch_solve", "sld_solve_batched"):
@@ -246,6 +252,19 @@ class System:
         if st != OK and raise_on_error:
             _check(st)
         return x, info
+
+    def solve_gmres(self, b=None, x=None, m=20, deflate=True, tol=1e-6, maxiter=5000, raise_on_error=True):
+        """PDGMRES (sld_solve_gmres): deflated right-Jacobi GMRES(m), FP64.
+        Returns (x, GmresInfo); status in info.status."""
+        if x is None:
+            x = np.empty(self.n, dtype=np.float64)
+        r = GmresInfo()
+        st = load().sld_solve_gmres(self._h, _ptr(b, np.float64), int(m), 1 if deflate else 0, float(tol),
+                                    int(maxiter), _ptr(x, np.float64), C.byref(r))
+        r.status = st
+        if st != OK and raise_on_error:
+            _check(st)
+        return x, r
 
     # -- per-step access ------------------------------------------------------
     def get_operator(self):

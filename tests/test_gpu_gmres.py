@@ -1,0 +1,124 @@
+"""PDGMRES on the GPU (sld_solve_gmres) against the CPU oracle of the same
+method: solutions, iteration counts (classical Gram-Schmidt twice on the GPU,
+modified Gram-Schmidt in the oracle: equal in exact arithmetic), the residual
+estimate against the recomputed residual, edge cases and errors.
+
+Restarted GMRES with short cycles is sensitive to rounding: on the 32^3 case
+GMRES(5) takes 730 steps, or 689 after a relative 1e-15 change of b.  The
+iteration count is therefore compared with the spread of the oracle over
+such perturbations (widened by 10 %), and tightly only for m = 20, where the
+count does not move."""
+import numpy as np
+import pytest
+
+from paper_1510_02148_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import oracle
+    from oracle import pdgmres
+    from paper_1510_02148_gb300 import _build, sld
+    _build.build()
+    sld.load()
+    oracle.build()
+    return sld, oracle, pdgmres
+
+
+def _system(sld, P):
+    s = sld.System(P.K.reshape(-1), P.q.reshape(-1), P.bc_type, P.bc_value, shape=P.shape)
+    s.make_labels(P.S, P.tau, P.L)
+    s.build_deflation(P.d)
+    return s
+
+
+CASES = [
+    ("lognormal 32^3, d=16", lambda: W.lognormal_point_source(32, 32, 32, 8, (2, 2, 2), seed=2)),
+    ("ragged 20x13x9", lambda: W.lognormal_point_source(20, 13, 9, 3, (2, 2, 1), seed=4)),
+]
+
+
+def _oracle_band(P_, A, lab, d, m, tol, b=None):
+    """(min, max) oracle step counts over b and three 1e-15 relative perturbations of it."""
+    b = A.b if b is None else b
+    its = []
+    for k in range(4):
+        bk = b if k == 0 else b * (1 + 1e-15 * np.random.default_rng(k).standard_normal(A.n))
+        its.append(P_.pdgmres(A, lab, d, b=bk, m=m, tol=tol, maxiter=20000).iterations)
+    return min(its), max(its)
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("m", [5, 20])
+@pytest.mark.parametrize("deflate", [True, False])
+def test_parity_with_oracle(env, case, m, deflate):
+    sld, oracle, P_ = env
+    P = case[1]()
+    A = oracle.assemble(P.K, P.q, P.bc_type, P.bc_value)
+    lab = oracle.labels(P.K, P.S, P.tau, P.L)
+    tol = 1e-10
+    ref = P_.pdgmres(A, lab if deflate else None, P.d if deflate else 0, m=m, tol=tol, maxiter=20000)
+    assert ref.status == P_.OK
+    s = _system(sld, P)
+    x, info = s.solve_gmres(m=m, deflate=deflate, tol=tol, maxiter=20000)
+    s.close()
+    assert info.true_relres <= 1.5 * tol
+    assert abs(info.relres_estimate - info.true_relres) <= 1e-3 * info.true_relres + 1e-14
+    assert np.linalg.norm(x - ref.x) / np.linalg.norm(ref.x) <= 1e-6
+    lo, hi = _oracle_band(P_, A, lab if deflate else None, P.d if deflate else 0, m, tol)
+    assert 0.9 * lo <= info.iterations <= 1.1 * hi, (info.iterations, lo, hi)
+    if m >= 20:
+        assert abs(info.iterations - ref.iterations) <= max(3, int(0.03 * ref.iterations)), \
+            (info.iterations, ref.iterations)
+    # the true residual through the oracle's own matrix
+    t = np.linalg.norm(A.b - A.spmv(x)) / np.linalg.norm(A.b)
+    assert abs(t - info.true_relres) <= 1e-3 * t + 1e-15
+
+
+def test_deflation_cuts_iterations(env):
+    sld, oracle, P_ = env
+    # 4 x 4 x 4 subdomains x 2 levelsets (d = 128): the oracle takes 52 steps
+    # deflated and 299 plain on this field
+    P = W.lognormal_point_source(32, 32, 32, 8, (4, 4, 4), seed=3)
+    s = _system(sld, P)
+    _, plain = s.solve_gmres(m=20, deflate=False, tol=1e-6, maxiter=20000)
+    _, defl = s.solve_gmres(m=20, deflate=True, tol=1e-6, maxiter=20000)
+    s.close()
+    assert defl.true_relres <= 1e-6 and plain.true_relres <= 1e-6
+    assert defl.iterations < 0.5 * plain.iterations, (defl.iterations, plain.iterations)
+
+
+def test_edge_cases_and_errors(env):
+    sld, oracle, P_ = env
+    P = W.lognormal_point_source(16, 16, 16, 4, (2, 2, 2), seed=5)
+    s = _system(sld, P)
+    # b = 0: x = 0 without iterating
+    x, info = s.solve_gmres(b=np.zeros(P.n), m=10)
+    assert info.iterations == 0 and not np.any(x)
+    # the iteration cap: NOT_CONVERGED, x and info still written
+    x, info = s.solve_gmres(m=10, tol=1e-14, maxiter=3, raise_on_error=False)
+    assert info.status == 3 and info.iterations == 3
+    assert np.all(np.isfinite(x)) and 0 < info.true_relres < 1
+    # GMRES(1): still a minimal-residual iteration, converges slowly but surely here
+    A = oracle.assemble(P.K, P.q, P.bc_type, P.bc_value)
+    lab = oracle.labels(P.K, P.S, P.tau, P.L)
+    ref = P_.pdgmres(A, lab, P.d, m=1, tol=1e-3, maxiter=3000)
+    x, info = s.solve_gmres(m=1, tol=1e-3, maxiter=3000, raise_on_error=False)
+    assert info.status == ref.status
+    lo, hi = _oracle_band(P_, A, lab, P.d, 1, 1e-3)
+    assert 0.9 * lo <= info.iterations <= 1.1 * hi, (info.iterations, lo, hi)
+    for bad in (dict(m=0), dict(m=32), dict(tol=0.0), dict(tol=1.0), dict(maxiter=0)):
+        with pytest.raises(sld.SldError, match="INVALID_ARG"):
+            s.solve_gmres(**bad)
+    s.close()
+    s2 = sld.System(P.K.reshape(-1), P.q.reshape(-1), P.bc_type, P.bc_value, shape=P.shape)
+    with pytest.raises(sld.SldError, match="STATE"):
+        s2.solve_gmres(deflate=True)
+    x, info = s2.solve_gmres(deflate=False, tol=1e-8, maxiter=20000)  # plain GMRES needs no deflation
+    assert info.true_relres <= 1.5e-8
+    s2.close()
