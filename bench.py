@@ -136,6 +136,42 @@ def cpu_baseline(P, A=None, lab=None, iters_full=None, sample_iters=40, threads=
                       f"scaled to {full} iterations"}
 
 
+def gmres_bytes(n, m, its, cycles, deflated):
+    """Algorithmic bytes of a PDGMRES solve: per Arnoldi step with basis size
+    j+1, apply 68 B (v, V_j, w, faces, diag, 1/diag, label), deflation 52 B
+    (w r/w, faces, diag, label), two dot passes (j+1) 8 + 8 B and two
+    orthogonalisation passes (j+1) 8 + 16 B; per cycle the residual (apply,
+    deflation, copy with norm: 68 + 52 + 16 B); plain GMRES drops the
+    deflation pass and the labels."""
+    per_step = (168 if deflated else 112)
+    per_cycle = (136 if deflated else 80)
+    tot = 0
+    left = its
+    for c in range(cycles):
+        k = min(m, left)
+        left -= k
+        tot += per_cycle + per_step * k + 32 * k * (k + 1) // 2
+    return n * tot
+
+
+def bench_gmres(sld, torch, s, x, P, m=20, tol=1e-6):
+    """PDGMRES(m) (the paper's solver: deflated right-Jacobi GMRES, FP64) on
+    the bench workload at the paper's tolerance, against plain GMRES(m)
+    (capped) and deflated CG to the same tolerance."""
+    out = {"m": m, "tol": tol, "precision": "fp64"}
+    for name, defl, cap in (("deflated", True, 20000), ("plain", False, 2000)):
+        s.solve_gmres(x=x, m=m, deflate=defl, tol=tol, maxiter=min(cap, 50), raise_on_error=False)  # warm-up
+        _, g = s.solve_gmres(x=x, m=m, deflate=defl, tol=tol, maxiter=cap, raise_on_error=False)
+        by = gmres_bytes(P.n, m, g.iterations, g.cycles, defl)
+        out[name] = {"iterations": g.iterations, "cycles": g.cycles, "ms": g.solve_ms,
+                     "converged": g.status == 0, "true_relres": g.true_relres,
+                     "ms_per_step": g.solve_ms / max(1, g.iterations),
+                     "alg_gbs": by / (g.solve_ms * 1e-3) / 1e9}
+    _, c = s.solve(x=x, precision=sld.FP64, tol=tol)
+    out["dpcg_fp64_same_tol"] = {"iterations": c.iterations, "ms": c.solve_ms}
+    return out
+
+
 def bench_batched(sld, torch, reps=3):
     """64 independent layered cubes (side ~ U{32..160}) in one batched
     persistent launch (FP32 inner, FP64 refinement), against the same
@@ -290,6 +326,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-gmres", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--profile-solve", choices=["fp64", "fp32_ir", "bf16"], default=None,
                     help="set up the workload and run one solve (for profiler captures); no timing line")
@@ -396,6 +433,8 @@ def main():
         line["batched"] = bench_batched(sld, torch)
     if not args.no_learned:
         line["learned"] = bench_learned(sld, torch)
+    if not args.no_gmres:
+        line["pdgmres"] = bench_gmres(sld, torch, s, x, P)
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(P, iters_full=fp64[-1].iterations, sample_iters=30)
     s.close()

@@ -54,32 +54,47 @@ __global__ void __launch_bounds__(kGT) k_gm_apply(SolveArgs a, const double* __r
   __syncthreads();
   double sc = 1.0;
   if constexpr (MODE == GM_PRECOND) sc = 1.0 / sqrt(*norm2);
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t nround = (a.g.n + stride - 1) / stride;
+  // each CTA takes one contiguous chunk of cells (a multiple of its size), so
+  // that a lane's label stays the same over many rounds and the label sums
+  // are flushed rarely
+  const int64_t chunk = ((a.g.n + gridDim.x - 1) / gridDim.x + blockDim.x - 1) / blockDim.x * blockDim.x;
+  const int64_t i_end = min(a.g.n, (int64_t)(blockIdx.x + 1) * chunk);
+  const int64_t nround = chunk / blockDim.x;
   CellWalk c;
-  c.init(a, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, stride);
+  c.init(a, (int64_t)blockIdx.x * chunk + threadIdx.x, blockDim.x);
   LabelAcc<double, WACC> la;
   la.init(a.lab_L);
-  for (int64_t rnd = 0; rnd < nround; ++rnd, c.next()) {
-    const bool ok = c.ok();
-    double wv = 0.0;
-    int l = -1;
-    if (ok) {
-      const int64_t i = c.i;
-      if constexpr (MODE == GM_PRECOND) {
-        wv = apply64(a, c, [&](int64_t j, int64_t) { return (v[j] * sc) * a.invdiag64[j]; });
-        vout[i] = v[i] * sc;
-      } else if constexpr (MODE == GM_RESID) {
-        wv = a.b[i] - apply64(a, c, [&](int64_t j, int64_t) { return v[j]; });
-      } else if constexpr (MODE == GM_APPLY) {
-        wv = apply64(a, c, [&](int64_t j, int64_t) { return v[j]; });
-      } else {
-        wv = v[i];
-      }
-      if constexpr (MODE != GM_COPY) w[i] = wv;
-      if (d > 0) l = a.label[i];
+  auto cell = [&](const CellWalk& cw, double& wv, int& l) {
+    const int64_t i = cw.i;
+    if constexpr (MODE == GM_PRECOND) {
+      wv = apply64(a, cw, [&](int64_t j, int64_t) { return (v[j] * sc) * a.invdiag64[j]; });
+      vout[i] = v[i] * sc;
+    } else if constexpr (MODE == GM_RESID) {
+      wv = a.b[i] - apply64(a, cw, [&](int64_t j, int64_t) { return v[j]; });
+    } else if constexpr (MODE == GM_APPLY) {
+      wv = apply64(a, cw, [&](int64_t j, int64_t) { return v[j]; });
+    } else {
+      wv = v[i];
     }
-    if (d > 0) la.add(ok, l, wv, sacc, d, warp);
+    if constexpr (MODE != GM_COPY) w[i] = wv;
+    if (d > 0) l = a.label[i];
+  };
+  // two rounds at a time (this round's cell and the next round's): more
+  // loads in flight; the label sums still take the cells in round order
+  for (int64_t rnd = 0; rnd < nround; rnd += 2) {
+    CellWalk c2 = c;
+    c2.next();
+    const bool ok0 = c.i < i_end, ok1 = rnd + 1 < nround && c2.i < i_end;
+    double w0 = 0.0, w1 = 0.0;
+    int l0 = -1, l1 = -1;
+    if (ok0) cell(c, w0, l0);
+    if (ok1) cell(c2, w1, l1);
+    if (d > 0) {
+      la.add(ok0, l0, w0, sacc, d, warp);
+      if (rnd + 1 < nround) la.add(ok1, l1, w1, sacc, d, warp);
+    }
+    c = c2;
+    c.next();
   }
   if (d > 0) {
     la.flush(sacc, d, warp);
@@ -122,8 +137,18 @@ __global__ void k_gm_gemv(int d, const double* __restrict__ Einv, const double* 
 __global__ void __launch_bounds__(kGT) k_gm_defl(SolveArgs a, const double* __restrict__ y, double* __restrict__ w) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   CellWalk c;
-  for (c.init(a, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, stride); c.ok(); c.next())
-    w[c.i] -= apply64(a, c, [&](int64_t j, int64_t) { return y[__ldg(a.label + j)]; });
+  c.init(a, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, stride);
+  while (c.ok()) {  // two cells per pass: more loads in flight
+    CellWalk c2 = c;
+    c2.next();
+    const double u0 = apply64(a, c, [&](int64_t j, int64_t) { return y[__ldg(a.label + j)]; });
+    double u1 = 0.0;
+    if (c2.ok()) u1 = apply64(a, c2, [&](int64_t j, int64_t) { return y[__ldg(a.label + j)]; });
+    w[c.i] -= u0;
+    if (c2.ok()) w[c2.i] -= u1;
+    c = c2;
+    c.next();
+  }
 }
 
 // Partial rows of V_k . w for the kGDots basis vectors k0 = blockIdx.y * kGDots ..
@@ -167,6 +192,7 @@ __global__ void __launch_bounds__(kGT) k_gm_orth(int64_t n, const double* __rest
   double nn = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     double t = w[i];
+#pragma unroll 4
     for (int k = 0; k < nv; ++k) t -= hs[k] * V[(int64_t)k * n + i];
     out[i] = t;
     nn += t * t;
@@ -191,6 +217,7 @@ __global__ void __launch_bounds__(kGT) k_gm_update(int64_t n, const double* __re
   __syncthreads();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     double t = 0.0;
+#pragma unroll 4
     for (int k = 0; k < nv; ++k) t += us[k] * V[(int64_t)k * n + i];
     xt[i] += invdiag[i] * t;
   }

@@ -260,15 +260,19 @@ __device__ void sweep_O1(const SolveArgs& a, double* sacc, double* red, double* 
   __syncthreads();
   double bb = 0.0;
   double sl[kMaxL] = {};  // Z_L^T r' (extra columns)
-  const int64_t stride = (int64_t)a.sy.ncta * blockDim.x;
-  const int64_t nround = (g.n + stride - 1) / stride;
+  // each CTA takes one contiguous chunk of cells (a multiple of its size):
+  // a lane's label then stays the same over many rounds, and the label sums
+  // are flushed rarely
+  const int64_t chunk = ((g.n + a.sy.ncta - 1) / a.sy.ncta + blockDim.x - 1) / blockDim.x * blockDim.x;
+  const int64_t i_end = min(g.n, (int64_t)(team_rank(a.sy) + 1) * chunk);
+  const int64_t nround = chunk / blockDim.x;
   CellWalk c;
-  c.init(a, (int64_t)team_rank(a.sy) * blockDim.x + threadIdx.x, stride);
+  c.init(a, (int64_t)team_rank(a.sy) * chunk + threadIdx.x, blockDim.x);
   LabelAcc<double, WACC> la;
   la.init(a.lab_L);
   for (int64_t rnd = 0; rnd < nround; ++rnd, c.next()) {
     const int64_t i = c.i;
-    const bool ok = c.ok();
+    const bool ok = i < i_end;
     double r = 0.0;
     int l = -1;
     if (ok) {
