@@ -140,6 +140,25 @@ sld_status sld_make_labels(sld_system s, int Sx, int Sy, int Sz, const double* t
                            int32_t* labels_out);
 
 /*
+ * Automatic subdomain-levelset labels: the regions of sld_make_labels (one
+ * per subdomain and levelset class) split into their face-connected
+ * components (6-neighbour, inside the subdomain), one label per component --
+ * Section 3.2.2's vectors built without manual input, the way the
+ * physics-based vectors of Section 4 take one vector per layer.  Numbering:
+ * components ordered by (sld_make_labels label, smallest cell index x-fastest
+ * of the component), labelled 0 .. d-1.
+ *   Sx, Sy, Sz, tau, L: as sld_make_labels (Sx*Sy*Sz*L <= 2^20).
+ *   labels_out: n int32 (host or device) or NULL.  d_out: the number of
+ *   components (host; also set when there are too many).
+ * The labels stay on the device for sld_build_deflation(s, NULL, *d_out, ...).
+ * Errors: SLD_ERR_INVALID_ARG (arguments; more than 4096 components, in which
+ * case the handle keeps the sld_make_labels labels), SLD_ERR_OOM,
+ * SLD_ERR_CUDA.
+ */
+sld_status sld_make_labels_cc(sld_system s, int Sx, int Sy, int Sz, const double* tau, int L,
+                              int32_t* labels_out, int* d_out);
+
+/*
  * Deflation space Z = [Z_lab, Z_extra] (Section 3.1, Def. 3.1): Z_lab has d
  * indicator columns (column labels[i] is 1 in row i), Z_extra k dense columns.
  * Builds E = Z^T A Z (eq. (E)) on the device, pins E_cc = 1 for an empty

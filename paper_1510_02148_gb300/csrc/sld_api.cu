@@ -259,7 +259,9 @@ sld_status sld_build_system(const double* K, const double* q, sld_grid g, sld_bc
   return SLD_OK;
 }
 
-sld_status sld_make_labels(sld_system s, int Sx, int Sy, int Sz, const double* tau, int L, int32_t* labels_out) {
+namespace {
+// the plain subdomain-levelset labels into s->label (argument checks included)
+sld_status plain_labels(sld_system s, int Sx, int Sy, int Sz, const double* tau, int L, int64_t dmax) {
   g_last_error.clear();
   if (!s) return fail(SLD_ERR_INVALID_ARG, "handle is NULL");
   if (Sx < 1 || Sy < 1 || Sz < 1 || Sx > s->g.nx || Sy > s->g.ny || Sz > s->g.nz)
@@ -267,7 +269,7 @@ sld_status sld_make_labels(sld_system s, int Sx, int Sy, int Sz, const double* t
   if (L < 1 || L > 16) return fail(SLD_ERR_INVALID_ARG, "L must be in [1, 16]");
   if (L > 1 && !tau) return fail(SLD_ERR_INVALID_ARG, "tau is NULL");
   const int64_t d = (int64_t)Sx * Sy * Sz * L;
-  if (d > sld::kMaxD) return fail(SLD_ERR_INVALID_ARG, "d = Sx*Sy*Sz*L exceeds " + std::to_string(sld::kMaxD));
+  if (d > dmax) return fail(SLD_ERR_INVALID_ARG, "d = Sx*Sy*Sz*L exceeds " + std::to_string(dmax));
   double htau[16] = {0};
   if (L > 1) {
     cudaError_t e = cudaMemcpy(htau, tau, sizeof(double) * (L - 1), is_device_ptr(tau) ? cudaMemcpyDeviceToHost
@@ -284,6 +286,11 @@ sld_status sld_make_labels(sld_system s, int Sx, int Sy, int Sz, const double* t
   s->have_labels_d = (int)d;
   s->labels_L = L;
   s->deflation_ready = false;
+  return SLD_OK;
+}
+
+sld_status labels_out_copy(sld_system s, int32_t* labels_out) {
+  cudaError_t e;
   if (labels_out) {
     if ((e = cudaMemcpyAsync(labels_out, s->label, sizeof(int32_t) * s->g.n, kind_out(labels_out), s->stream)) !=
         cudaSuccess)
@@ -291,6 +298,31 @@ sld_status sld_make_labels(sld_system s, int Sx, int Sy, int Sz, const double* t
   }
   if ((e = cudaStreamSynchronize(s->stream)) != cudaSuccess) return cuda_fail(e, "labels");
   return SLD_OK;
+}
+
+}  // namespace
+
+sld_status sld_make_labels(sld_system s, int Sx, int Sy, int Sz, const double* tau, int L, int32_t* labels_out) {
+  g_last_error.clear();
+  sld_status st = plain_labels(s, Sx, Sy, Sz, tau, L, sld::kMaxD);
+  if (st != SLD_OK) return st;
+  return labels_out_copy(s, labels_out);
+}
+
+sld_status sld_make_labels_cc(sld_system s, int Sx, int Sy, int Sz, const double* tau, int L, int32_t* labels_out,
+                              int* d_out) {
+  g_last_error.clear();
+  if (!d_out) return fail(SLD_ERR_INVALID_ARG, "d_out is NULL");
+  sld_status st = plain_labels(s, Sx, Sy, Sz, tau, L, 1 << 20);
+  if (st != SLD_OK) return st;
+  std::string msg;
+  int d = 0;
+  const int code = sld::run_cc_labels(s, s->have_labels_d, sld::kMaxD, &d, &msg);
+  *d_out = d;
+  if (code != SLD_OK) return fail((sld_status)code, msg);
+  s->have_labels_d = d;
+  s->labels_L = 0;  // component labels have no subdomain * L + class structure
+  return labels_out_copy(s, labels_out);
 }
 
 sld_status sld_build_deflation(sld_system s, const int32_t* labels, int d, const void* Zextra, int k,

@@ -167,6 +167,10 @@ cudaError_t tma_batch_launch(int G, size_t smem, unsigned args_off, bool wacc, c
 int launch_solve_tma_learned(sld_system s, SolveArgs& a, const sld_options& o, float* ms, std::string* msg);
 // sld_api.cu: the thread-local message returned by sld_last_error()
 void set_last_error(const std::string& msg);
+// sld_cc.cu: split the plain labels in s->label (d0 values) into connected
+// components, renumbered canonically in place; *d_out = component count (the
+// labels are left unchanged when it exceeds maxd).  Returns an sld_status.
+int run_cc_labels(sld_system s, int d0, int maxd, int* d_out, std::string* msg);
 // sld_gmres.cu: PDGMRES (deflated right-Jacobi restarted GMRES, FP64);
 // b: device.  Writes the solution to s->x.  Returns an sld_status.
 int run_gmres(sld_system s, const double* b, int m, int deflate, double tol, int maxiter, sld_gmres_info* info,

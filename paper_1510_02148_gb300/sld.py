@@ -33,7 +33,8 @@ EXPORTED = ["sld_default_options", "sld_build_system", "sld_make_labels", "sld_b
             "sld_batch_describe", "sld_batch_destroy", "sld_solve_batched", "sld_deflation_info",
             "sld_net_num_params", "sld_net_create", "sld_net_set_params", "sld_net_get_params",
             "sld_net_get_grads", "sld_net_forward", "sld_net_backward", "sld_net_loss_backward",
-            "sld_net_adam", "sld_net_destroy", "sld_lanczos_eigvecs", "sld_solve_gmres"]
+            "sld_net_adam", "sld_net_destroy", "sld_lanczos_eigvecs", "sld_solve_gmres",
+            "sld_make_labels_cc"]
 
 
 class SldError(RuntimeError):
@@ -114,6 +115,7 @@ def load(path: str = LIB_PATH):
         lib.sld_net_destroy.argtypes = [P]
         lib.sld_net_destroy.restype = None
         lib.sld_lanczos_eigvecs.argtypes = [P, C.c_int, C.c_int, P, P, P]
+        lib.sld_make_labels_cc.argtypes = [P, C.c_int, C.c_int, C.c_int, P, C.c_int, P, C.POINTER(C.c_int)]
         lib.sld_solve_gmres.argtypes = [P, P, C.c_int, C.c_int, C.c_double, C.c_int, P, C.POINTER(GmresInfo)]
         for name in ("sld_build_system", "sld_make_labels", "sld_build_deflation", "sld_solve",
                      "sld_get_operator", "sld_apply_A", "sld_restrict", "sld_get_coarse",
@@ -216,6 +218,20 @@ class System:
         _check(load().sld_make_labels(self._h, int(S[0]), int(S[1]), int(S[2]), _ptr(tau_a, np.float64),
                                       int(L), _ptr(out, np.int32)))
         return out
+
+    def make_labels_cc(self, S, tau, L, out=None):
+        """Automatic subdomain-levelset labels (sld_make_labels_cc): the
+        connected components of each subdomain's levelset classes.  Returns
+        (labels, d); follow with build_deflation(d)."""
+        tau_a = np.ascontiguousarray(tau if len(tau) else [0.0], dtype=np.float64)
+        if out is None:
+            out = np.empty(self.n, dtype=np.int32)
+        d = C.c_int(0)
+        st = load().sld_make_labels_cc(self._h, int(S[0]), int(S[1]), int(S[2]), _ptr(tau_a, np.float64), int(L),
+                                       _ptr(out, np.int32), C.byref(d))
+        self.cc_components = d.value
+        _check(st)
+        return out, d.value
 
     def build_deflation(self, d, labels=None, Zextra=None):
         """Z = [label columns, Zextra]: Zextra is n x k (k <= 8), row-major,
