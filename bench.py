@@ -172,6 +172,29 @@ def bench_gmres(sld, torch, s, x, P, m=20, tol=1e-6):
     return out
 
 
+def bench_auto_labels(sld, torch, P, x):
+    """The same workload deflated with the automatic subdomain-levelset
+    labels (face-connected components of each subdomain's levelset classes)
+    instead of the plain ones: label construction time, d, and the
+    FP32-inner and FP64 solves."""
+    s = sld.System(torch.from_numpy(P.K.reshape(-1)).cuda(), torch.from_numpy(P.q.reshape(-1)).cuda(),
+                   P.bc_type, P.bc_value, shape=P.shape)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, d = s.make_labels_cc(P.S, P.tau, P.L)
+    torch.cuda.synchronize()
+    lab_ms = (time.perf_counter() - t0) * 1e3
+    s.build_deflation(d)
+    out = {"d": d, "d_plain": P.d, "labels_ms": lab_ms}
+    for name, prec in (("fp32_ir", sld.FP32_IR), ("fp64", sld.FP64)):
+        s.solve(x=x, precision=prec)
+        _, i = s.solve(x=x, precision=prec)
+        out[name] = {"ms": i.solve_ms, "iterations": i.iterations, "outer_steps": i.outer_steps,
+                     "true_relres": i.true_relres}
+    s.close()
+    return out
+
+
 def bench_batched(sld, torch, reps=3):
     """64 independent layered cubes (side ~ U{32..160}) in one batched
     persistent launch (FP32 inner, FP64 refinement), against the same
@@ -327,6 +350,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-gmres", action="store_true")
+    ap.add_argument("--no-auto-labels", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--profile-solve", choices=["fp64", "fp32_ir", "bf16"], default=None,
                     help="set up the workload and run one solve (for profiler captures); no timing line")
@@ -435,6 +459,8 @@ def main():
         line["learned"] = bench_learned(sld, torch)
     if not args.no_gmres:
         line["pdgmres"] = bench_gmres(sld, torch, s, x, P)
+    if not args.no_auto_labels:
+        line["auto_labels"] = bench_auto_labels(sld, torch, P, x)
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(P, iters_full=fp64[-1].iterations, sample_iters=30)
     s.close()
