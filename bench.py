@@ -195,6 +195,31 @@ def bench_auto_labels(sld, torch, P, x):
     return out
 
 
+def bench_spe10(sld, torch):
+    """The paper's SPE10 sweep of plain subdomain deflation (d = 8, 27, 64,
+    and d = 1 for reference) on the deflated-CG path, on an SPE10-shaped
+    synthetic field (180x220x85): FP32-inner solves to 1e-9."""
+    from paper_1510_02148_gb300 import workloads as W
+    P = W.spe10_like()
+    Kd = torch.from_numpy(P.K.reshape(-1)).cuda()
+    qd = torch.from_numpy(P.q.reshape(-1)).cuda()
+    s = sld.System(Kd, qd, P.bc_type, P.bc_value, shape=P.shape)
+    x = torch.empty(P.n, dtype=torch.float64, device="cuda")
+    out = {"workload": f"SPE10-shaped synthetic {P.shape[2]}x{P.shape[1]}x{P.shape[0]} ({P.n} cells)", "runs": []}
+    for S in ((1, 1, 1), (2, 2, 2), (3, 3, 3), (4, 4, 4)):
+        d = S[0] * S[1] * S[2]
+        s.make_labels(S, (), 1)
+        s.build_deflation(d)
+        row = {"d": d}
+        for name, prec in (("fp32_ir", sld.FP32_IR),):
+            s.solve(x=x, precision=prec, raise_on_error=False)
+            _, i = s.solve(x=x, precision=prec, raise_on_error=False)
+            row[name] = {"ms": i.solve_ms, "iterations": i.iterations, "true_relres": i.true_relres}
+        out["runs"].append(row)
+    s.close()
+    return out
+
+
 def bench_batched(sld, torch, reps=3):
     """64 independent layered cubes (side ~ U{32..160}) in one batched
     persistent launch (FP32 inner, FP64 refinement), against the same
@@ -351,6 +376,7 @@ def main():
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-gmres", action="store_true")
     ap.add_argument("--no-auto-labels", action="store_true")
+    ap.add_argument("--no-spe10", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--profile-solve", choices=["fp64", "fp32_ir", "bf16"], default=None,
                     help="set up the workload and run one solve (for profiler captures); no timing line")
@@ -461,6 +487,8 @@ def main():
         line["pdgmres"] = bench_gmres(sld, torch, s, x, P)
     if not args.no_auto_labels:
         line["auto_labels"] = bench_auto_labels(sld, torch, P, x)
+    if not args.no_spe10:
+        line["spe10_like"] = bench_spe10(sld, torch)
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(P, iters_full=fp64[-1].iterations, sample_iters=30)
     s.close()

@@ -189,3 +189,54 @@ def sandwich_theorem(nx=4, ny=4, nz=12, n_layers=6, eps=1e-6) -> Problem:
     bct = (NOFLOW, NOFLOW, NOFLOW, NOFLOW, NOFLOW, DIRICHLET)
     return Problem(f"theorem{nx}x{ny}x{nz}", K, None, bct, (0, 0, 0, 0, 0, 0.0),
                    S=(1, 1, n_layers), tau=(math.sqrt(eps),), L=2)
+
+
+def _smooth2(a, passes=3, w=5):
+    """Separable box smoothing in the last two axes (x and y), `passes` times."""
+    k = np.ones(w) / w
+    for _ in range(passes):
+        a = np.apply_along_axis(lambda v: np.convolve(v, k, mode="same"), -1, a)
+        a = np.apply_along_axis(lambda v: np.convolve(v, k, mode="same"), -2, a)
+    return a
+
+
+def spe10_like(nx=180, ny=220, nz=85, S=(2, 2, 2), seed=1) -> Problem:
+    """An SPE10-shaped synthetic field (the SPE10 data are not used): the top
+    35/85 of the layers a smooth, strongly varying lognormal field (log10 K
+    spread ~ 4 decades, like the Tarbert formation), the rest fluvial: sinuous
+    high-permeability channels (~1e3) a few cells wide and a few layers thick
+    in a low-permeability background (~1e-2), like the Upper Ness; clipped to
+    [1e-3, 10^4.5], about SPE10's 7.5 decades.  Dirichlet
+    x-faces, a unit source at the centre cell, plain subdomain deflation
+    (L = 1: one vector per subdomain, d = Sx * Sy * Sz), as in the paper's
+    SPE10 runs with d = 8, 27, 64."""
+    rng = np.random.default_rng(seed)
+    ntop = int(round(nz * 35 / 85))
+    K = np.empty((nz, ny, nx))
+    g = _smooth2(rng.standard_normal((nz, ny, nx)), passes=2, w=5)
+    g = (g - g.mean()) / g.std()
+    # top: lognormal, log10 K ~ N(1, 1.2^2)
+    K[nz - ntop:] = 10.0 ** (1.0 + 1.2 * g[nz - ntop:])
+    # bottom: background, then channels
+    nb = nz - ntop
+    K[:nb] = 10.0 ** (-2.0 + 0.3 * g[:nb])
+    y = np.arange(ny)
+    xg = np.arange(nx)[None, :]
+    z = 0
+    while z < nb:
+        thick = int(rng.integers(2, 6))
+        for _ in range(int(rng.integers(2, 6))):
+            x0 = rng.uniform(0, nx)
+            amp = rng.uniform(0.05, 0.2) * nx
+            lam = rng.uniform(0.3, 1.0) * ny
+            ph = rng.uniform(0, 2 * np.pi)
+            width = rng.uniform(2.0, 0.06 * nx + 3.0)
+            xc = x0 + amp * np.sin(2 * np.pi * y / lam + ph)
+            inside = np.abs(xg - xc[:, None]) < width / 2
+            for dz in range(thick):
+                if z + dz < nb:
+                    K[z + dz][inside] = 10.0 ** (3.0 + 0.3 * g[z + dz][inside])
+        z += thick + int(rng.integers(0, 3))
+    # SPE10's permeabilities span about 7.5 decades
+    K = np.clip(K, 1e-3, 10.0 ** 4.5)
+    return Problem(f"spe10like{nx}x{ny}x{nz}", K, point_source(nx, ny, nz), *X_DIRICHLET, S=S, tau=(), L=1)
