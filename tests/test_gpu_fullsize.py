@@ -2,7 +2,9 @@
 checked through quantities the oracle computes at any size: the labels
 (bit-exact), and the FP64 true residual of the GPU solution evaluated with the
 oracle's own assembled matrix.  Plus the coarse sizes above the per-warp
-accumulator limit (d > 256) against the full oracle solve on a smaller grid."""
+accumulator limit (d > 256) against the full oracle solve on a smaller grid,
+and the next rows at their bench sizes: PDGMRES, the automatic labels, the
+SPE10-shaped workload."""
 import numpy as np
 import pytest
 
@@ -77,3 +79,47 @@ def test_large_d_parity(sld, oracle_mod):
     with pytest.raises(sld.SldError, match="d must be"):
         s.build_deflation(4097)
     s.close()
+
+
+def test_pdgmres_fullsize(sld, oracle_mod):
+    """PDGMRES(20) on the bench workload at the paper's tolerance: the
+    residual through the oracle's matrix, and the Givens estimate equal to it."""
+    P = W.lognormal_point_source()
+    s = sld.from_problem(P)
+    x, info = s.solve_gmres(m=20, tol=1e-6, maxiter=20000)
+    s.close()
+    A = oracle_mod.assemble(P.K, P.q, P.bc_type, P.bc_value)
+    t = _true_relres(A, x)
+    assert t <= 1e-6 and abs(t - info.true_relres) <= 1e-3 * t
+    assert abs(info.relres_estimate - t) <= 1e-3 * t
+
+
+def test_automatic_labels_fullsize(sld, oracle_mod):
+    """The automatic labels of the bench workload bit-exact against the
+    oracle's, and the FP32-inner solve with them to 1e-9 through the
+    oracle's matrix."""
+    from oracle import sld_cc
+    P = W.lognormal_point_source()
+    ref, dref = sld_cc.cc_labels(P.K, P.S, P.tau, P.L)
+    s = sld.System(P.K.reshape(-1), P.q.reshape(-1), P.bc_type, P.bc_value, shape=P.shape)
+    lab, d = s.make_labels_cc(P.S, P.tau, P.L)
+    assert d == dref and np.array_equal(lab, ref)
+    s.build_deflation(d)
+    x, info = s.solve(precision=sld.FP32_IR)
+    s.close()
+    A = oracle_mod.assemble(P.K, P.q, P.bc_type, P.bc_value)
+    assert _true_relres(A, x) <= 1e-9
+
+
+def test_spe10_like_fullsize(sld, oracle_mod):
+    """The SPE10-shaped sweep's workload (180x220x85) with d = 64: labels
+    bit-exact, the FP32-inner solve to 1e-9 through the oracle's matrix."""
+    P = W.spe10_like(S=(4, 4, 4))
+    s = sld.System(P.K.reshape(-1), P.q.reshape(-1), P.bc_type, P.bc_value, shape=P.shape)
+    lab = s.make_labels(P.S, P.tau, P.L)
+    assert np.array_equal(lab, oracle_mod.labels(P.K, P.S, P.tau, P.L))
+    s.build_deflation(P.d)
+    x, info = s.solve(precision=sld.FP32_IR)
+    s.close()
+    A = oracle_mod.assemble(P.K, P.q, P.bc_type, P.bc_value)
+    assert _true_relres(A, x) <= 1e-9
