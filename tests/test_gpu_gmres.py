@@ -122,3 +122,22 @@ def test_edge_cases_and_errors(env):
     x, info = s2.solve_gmres(deflate=False, tol=1e-8, maxiter=20000)  # plain GMRES needs no deflation
     assert info.true_relres <= 1.5e-8
     s2.close()
+
+
+def test_large_d_shared_atomic_label_sums(env):
+    """d = 512 label columns (above the per-warp accumulator limit of 256:
+    the label sums go through shared-memory atomics): PDGMRES(20) against
+    the oracle."""
+    sld, oracle, P_ = env
+    P = W.lognormal_point_source(64, 64, 32, 8, (8, 8, 4), seed=6)
+    assert P.d == 512
+    A = oracle.assemble(P.K, P.q, P.bc_type, P.bc_value)
+    lab = oracle.labels(P.K, P.S, P.tau, P.L)
+    ref = P_.pdgmres(A, lab, P.d, m=20, tol=1e-8, maxiter=20000)
+    s = _system(sld, P)
+    x, info = s.solve_gmres(m=20, tol=1e-8, maxiter=20000)
+    s.close()
+    assert info.true_relres <= 1.5e-8
+    assert np.linalg.norm(x - ref.x) / np.linalg.norm(ref.x) <= 1e-5
+    assert abs(info.iterations - ref.iterations) <= max(3, int(0.03 * ref.iterations)), \
+        (info.iterations, ref.iterations)
