@@ -175,8 +175,8 @@ def bench_gmres(sld, torch, s, x, P, m=20, tol=1e-6):
 def bench_auto_labels(sld, torch, P, x):
     """The same workload deflated with the automatic subdomain-levelset
     labels (face-connected components of each subdomain's levelset classes)
-    instead of the plain ones: label construction time, d, and the
-    FP32-inner and FP64 solves."""
+    instead of the plain ones: label construction time, d, the FP32-inner
+    and FP64 solves, and PDGMRES(20) to 1e-6."""
     s = sld.System(torch.from_numpy(P.K.reshape(-1)).cuda(), torch.from_numpy(P.q.reshape(-1)).cuda(),
                    P.bc_type, P.bc_value, shape=P.shape)
     torch.cuda.synchronize()
@@ -191,6 +191,10 @@ def bench_auto_labels(sld, torch, P, x):
         _, i = s.solve(x=x, precision=prec)
         out[name] = {"ms": i.solve_ms, "iterations": i.iterations, "outer_steps": i.outer_steps,
                      "true_relres": i.true_relres}
+    # PDGMRES(20) with these vectors, at the paper's tolerance
+    _, g = s.solve_gmres(x=x, m=20, tol=1e-6, maxiter=20000, raise_on_error=False)
+    out["pdgmres_m20_tol1e-6"] = {"ms": g.solve_ms, "iterations": g.iterations, "converged": g.status == 0,
+                                  "true_relres": g.true_relres}
     s.close()
     return out
 
