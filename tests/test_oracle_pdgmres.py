@@ -2,8 +2,9 @@
 restarted GMRES, Section 3.2 with the subdomain-levelset vectors of Section
 3.2.2): against dense direct solves, the minimal-residual definition of a
 GMRES iterate solved by dense least squares on an explicit Krylov basis,
-the Arnoldi relation, finite termination, and the projection identities.
-CPU only."""
+SciPy's restarted GMRES on the same (deflated, right-preconditioned)
+operator, the Arnoldi relation, finite termination, and the projection
+identities.  CPU only."""
 import numpy as np
 import pytest
 
@@ -42,9 +43,9 @@ def test_matches_dense_direct_solve(gm, m, defl):
 @pytest.mark.parametrize("defl", [False, True])
 def test_iterates_minimise_the_residual_over_the_krylov_space(gm, defl):
     """GMRES by definition: after j steps of the first cycle the residual is
-    min ||r0 - B M^{-1}... || over the Krylov space of B = P1 A M^{-1}; here
-    computed by dense least squares on the explicit (unorthogonalised)
-    Krylov basis [r0, B r0, ..., B^{j-1} r0]."""
+    the minimum of ||r0 - B K_j c|| over c, B = P1 A M^{-1}, K_j the explicit
+    (unorthogonalised) Krylov basis [r0, B r0, ..., B^{j-1} r0]; here by
+    dense least squares."""
     oracle, P = gm
     K, A, lab, d = _case(oracle, shape=(4, 5, 6), seed=7)
     Ad = A.dense()
@@ -125,3 +126,31 @@ def test_zero_rhs_and_iteration_cap(gm):
     capped = P.pdgmres(A, lab, d, m=10, tol=1e-14, maxiter=3)
     assert capped.status == P.NOT_CONVERGED and capped.iterations == 3
     assert np.all(np.isfinite(capped.x)) and capped.true_relres < 1.0
+
+
+@pytest.mark.parametrize("defl", [False, True])
+def test_history_matches_scipy_gmres_on_the_same_operator(gm, defl):
+    """SciPy's restarted GMRES (no preconditioner of its own) on the operator
+    B = P1 A M^{-1} with right-hand side P1 b minimises the same residual as
+    PDGMRES; its per-step residual norms (callback 'pr_norm', relative to
+    ||P1 b||) match the oracle's first cycles."""
+    import scipy.sparse.linalg as sla
+    oracle, P = gm
+    K, A, lab, d = _case(oracle, shape=(6, 7, 8), seed=9)
+    Ad = A.dense()
+    Minv = 1.0 / A.diag()
+    if defl:
+        Z = np.eye(d)[lab]
+        P1 = np.eye(A.n) - Ad @ Z @ np.linalg.solve(Z.T @ Ad @ Z, Z.T)
+    else:
+        P1 = np.eye(A.n)
+    B = P1 @ Ad * Minv[None, :]
+    rhs = P1 @ A.b
+    hist = []
+    sla.gmres(sla.aslinearoperator(B), rhs, rtol=1e-12, atol=0.0, restart=10, maxiter=3,
+              callback=lambda r: hist.append(r), callback_type="pr_norm")
+    res = P.pdgmres(A, lab if defl else None, d if defl else 0, m=10, tol=1e-12, maxiter=30)
+    bn = np.linalg.norm(A.b)
+    ours = res.hist[1:1 + len(hist)] * bn / np.linalg.norm(rhs)
+    k = min(len(hist), 25)
+    np.testing.assert_allclose(ours[:k], np.array(hist[:k]), rtol=1e-6, atol=1e-13)
