@@ -309,7 +309,8 @@ int run_gmres(sld_system s, const double* b, int m, int deflate, double tol, int
     k_gm_dots<<<dim3(G, (nv + kGDots - 1) / kGDots), kGT, 0, st>>>(n, V, nv, w, part, ps);
     colsum(nv, out);
   };
-  std::vector<double> H((size_t)(m + 1) * m), R((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), u(m);
+  // R: the Hessenberg matrix with the rotations applied (upper triangular part used)
+  std::vector<double> R((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), u(m);
   cudaEventRecord(s->ev0, st);
   // ||b||, and x* = Z y0 with y0 = E^{-1} Z^T b
   k_gm_orth<<<G, kGT, 0, st>>>(n, V, 0, sc->h1, b, raw, part, ps, 0);
@@ -372,9 +373,9 @@ int run_gmres(sld_system s, const double* b, int m, int deflate, double tol, int
       if (!fetch()) break;
       // Hessenberg column j, the earlier rotations, a new one for row j+1
       std::vector<double> col(j + 2);
-      for (int i = 0; i <= j; ++i) col[i] = H[(size_t)i * m + j] = hs.h1[i] + hs.h2[i];
+      for (int i = 0; i <= j; ++i) col[i] = hs.h1[i] + hs.h2[i];
       const double hn = std::sqrt(hs.nn);
-      col[j + 1] = H[(size_t)(j + 1) * m + j] = hn;
+      col[j + 1] = hn;
       for (int i = 0; i < j; ++i) {
         const double t = cs[i] * col[i] + sn[i] * col[i + 1];
         col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
