@@ -1,0 +1,38 @@
+/* A plain C client of libsld: compiled with gcc against include/sld.h and
+ * linked to the library, it checks what needs no GPU -- the defaults and the
+ * argument checks, which return status codes and set sld_last_error(). */
+#include <stdio.h>
+#include <string.h>
+
+#include "sld.h"
+#include "sld_net.h"
+
+static int fails = 0;
+#define CHECK(c)                                        \
+  do {                                                  \
+    if (!(c)) {                                         \
+      fprintf(stderr, "check failed: %s (line %d)\n", #c, __LINE__); \
+      ++fails;                                          \
+    }                                                   \
+  } while (0)
+
+int main(void) {
+  sld_options o;
+  memset(&o, 0xff, sizeof o);
+  sld_default_options(&o);
+  CHECK(o.precision == SLD_FP64);
+  CHECK(o.tol == 1e-9);
+  CHECK(o.maxiter == 20000 && o.max_outer == 40 && o.ctas_per_sm == 0);
+  CHECK(o.debug_skip_barrier == -1);
+  /* argument checks happen before any device work */
+  double x = 0.0;
+  CHECK(sld_solve(NULL, NULL, &o, &x, NULL) == SLD_ERR_INVALID_ARG);
+  CHECK(strlen(sld_last_error()) > 0);
+  CHECK(sld_solve_gmres(NULL, NULL, 20, 1, 1e-6, 100, &x, NULL) == SLD_ERR_INVALID_ARG);
+  int d = -1;
+  CHECK(sld_make_labels_cc(NULL, 1, 1, 1, NULL, 1, NULL, &d) == SLD_ERR_INVALID_ARG);
+  CHECK(sld_net_num_params() > 0);
+  sld_destroy(NULL); /* ignored */
+  printf("%s\n", fails ? "FAIL" : "OK");
+  return fails ? 1 : 0;
+}

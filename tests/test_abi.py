@@ -55,3 +55,18 @@ def test_binding_fails_loudly_without_library(tmp_path):
         ROOT, str(tmp_path / "missing.so"))
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True)
     assert "raised" in out.stdout, out.stdout + out.stderr
+
+
+def test_plain_c_client(libpath, tmp_path):
+    """The ABI is usable from C: a gcc-built client links libsld and gets the
+    defaults and the status codes of the argument checks (no GPU needed)."""
+    import subprocess
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    libdir = os.path.dirname(libpath)
+    exe = str(tmp_path / "abi_client")
+    subprocess.run(["gcc", "-std=c11", "-Wall", "-Werror", "-I", os.path.join(root, "include"),
+                    os.path.join(root, "tests", "c", "abi_client.c"), "-o", exe, "-L", libdir, "-lsld",
+                    "-Wl,-rpath," + libdir], check=True, capture_output=True)
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert r.stdout.strip() == "OK"
