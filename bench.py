@@ -298,7 +298,12 @@ def bench_learned(sld, torch, nfields=4):
         ku = s.deflation_info()[2]
         s.solve(x=x, precision=sld.FP32_IR)
         _, lrn = s.solve(x=x, precision=sld.FP32_IR)
-        rows.append((f64, f32, lrn, setup_ms, ku))
+        # the automatic labels (connected components of the levelset classes) instead
+        _, dcc = s.make_labels_cc(P.S, P.tau, P.L)
+        s.build_deflation(dcc)
+        s.solve(x=x, precision=sld.FP32_IR)
+        _, cc = s.solve(x=x, precision=sld.FP32_IR)
+        rows.append((f64, f32, lrn, setup_ms, ku, cc, dcc))
         s.close()
     net.close()
     med = lambda v: float(statistics.median(v))  # noqa: E731
@@ -312,7 +317,10 @@ def bench_learned(sld, torch, nfields=4):
             "learned_setup_ms": med([r[3] for r in rows]), "k_used": [r[4] for r in rows],
             "max_true_relres": max(r[2].true_relres for r in rows),
             "speedup_learned_vs_fp64_plain": med([r[0].solve_ms / r[2].solve_ms for r in rows]),
-            "speedup_learned_vs_fp32ir_plain": med([r[1].solve_ms / r[2].solve_ms for r in rows])}
+            "speedup_learned_vs_fp32ir_plain": med([r[1].solve_ms / r[2].solve_ms for r in rows]),
+            "fp32ir_auto_labels_ms": med([r[5].solve_ms for r in rows]),
+            "fp32ir_auto_labels_its": med([r[5].iterations for r in rows]),
+            "auto_labels_d": [r[6] for r in rows]}
 
 
 def run_reference(args):
