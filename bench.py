@@ -31,7 +31,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "time-to-1e-9 rel. residual & HBM GB/s: mixed/learned/batched vs plain FP64"
 WORKLOAD = "lognormal-layered 256x256x128, point source, 4x4x4 subdomains x 2 levelsets (d=128), tol 1e-9"
-# algorithmic bytes per cell (see DESIGN.md): one inner iteration (sweeps A
+# algorithmic bytes per cell: one inner iteration (sweeps A
 # and B) and one FP64 refinement step (sweeps O1 and O2).  The TMA sweeps
 # stream 16-bit labels.
 BYTES_ITER_FP32 = 60   # A: z, p_old, 3 faces, label, p_new  B: p, label, 3 faces, z r/w, xhat r/w
