@@ -238,6 +238,21 @@ typedef struct {
 sld_status sld_solve_gmres(sld_system s, const double* b, int m, int deflate, double tol, int maxiter,
                            double* x, sld_gmres_info* info);
 
+/*
+ * Harmonic Ritz pairs of an Arnoldi cycle (host computation; Section 3.2.1,
+ * eq. (defleig) form (a)): with the (m+1) x m Hessenberg matrix Hbar of m
+ * Arnoldi steps, F = H_m + h_{m+1,m}^2 H_m^{-T} e_m e_m^T, F y = theta y;
+ * the d pairs of smallest |theta| (a complex-conjugate pair as the real and
+ * imaginary parts of y, the next two columns).  The deflation vectors are
+ * z = V_m y.  Eigenvalues by the Francis double-shift QR iteration, vectors
+ * by inverse iteration.
+ *   Hbar: (m+1) x m, row-major, host.  2 <= m <= 64, 1 <= d <= m.
+ *   Y: m x d row-major (host, output); theta_re, theta_im: d values (host).
+ * Errors: SLD_ERR_INVALID_ARG, SLD_ERR_BREAKDOWN (singular H_m or no
+ * convergence of the QR iteration).
+ */
+sld_status sld_harmonic_ritz(const double* Hbar, int m, int d, double* Y, double* theta_re, double* theta_im);
+
 /* Release the handle and its device memory.  NULL is ignored. */
 void sld_destroy(sld_system s);
 

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsld.so")
 SOURCES = ["sld_api.cu", "sld_setup.cu", "sld_solve.cu", "sld_solve_tma.cu", "sld_solve_tma_learned.cu",
-           "sld_noalloc.cu", "sld_net.cu", "sld_lanczos.cu", "sld_gmres.cu", "sld_cc.cu"]
+           "sld_noalloc.cu", "sld_net.cu", "sld_lanczos.cu", "sld_gmres.cu", "sld_cc.cu", "sld_hritz.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xptxas", "-warn-spills"]

@@ -171,6 +171,8 @@ void set_last_error(const std::string& msg);
 // components, renumbered canonically in place; *d_out = component count (the
 // labels are left unchanged when it exceeds maxd).  Returns an sld_status.
 int run_cc_labels(sld_system s, int d0, int maxd, int* d_out, std::string* msg);
+// sld_hritz.cu: harmonic Ritz pairs (host); returns an sld_status
+int harmonic_ritz(const double* Hbar, int m, int d, double* Y, double* theta_re, double* theta_im);
 // sld_gmres.cu: PDGMRES (deflated right-Jacobi restarted GMRES, FP64);
 // b: device.  Writes the solution to s->x.  Returns an sld_status.
 int run_gmres(sld_system s, const double* b, int m, int deflate, double tol, int maxiter, sld_gmres_info* info,

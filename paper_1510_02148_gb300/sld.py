@@ -34,7 +34,7 @@ EXPORTED = ["sld_default_options", "sld_build_system", "sld_make_labels", "sld_b
             "sld_net_num_params", "sld_net_create", "sld_net_set_params", "sld_net_get_params",
             "sld_net_get_grads", "sld_net_forward", "sld_net_backward", "sld_net_loss_backward",
             "sld_net_adam", "sld_net_destroy", "sld_lanczos_eigvecs", "sld_solve_gmres",
-            "sld_make_labels_cc"]
+            "sld_make_labels_cc", "sld_harmonic_ritz"]
 
 
 class SldError(RuntimeError):
@@ -116,6 +116,7 @@ def load(path: str = LIB_PATH):
         lib.sld_net_destroy.restype = None
         lib.sld_lanczos_eigvecs.argtypes = [P, C.c_int, C.c_int, P, P, P]
         lib.sld_make_labels_cc.argtypes = [P, C.c_int, C.c_int, C.c_int, P, C.c_int, P, C.POINTER(C.c_int)]
+        lib.sld_harmonic_ritz.argtypes = [P, C.c_int, C.c_int, P, P, P]
         lib.sld_solve_gmres.argtypes = [P, P, C.c_int, C.c_int, C.c_double, C.c_int, P, C.POINTER(GmresInfo)]
         for name in ("sld_build_system", "sld_make_labels", "sld_build_deflation", "sld_solve",
                      "sld_get_operator", "sld_apply_A", "sld_restrict", "sld_get_coarse",
@@ -307,6 +308,20 @@ class System:
         Einv = np.empty((D, D))
         _check(load().sld_get_coarse(self._h, E.ctypes.data, Einv.ctypes.data))
         return E, Einv
+
+
+def harmonic_ritz(Hbar, d):
+    """(Y, theta) from sld_harmonic_ritz: Hbar (m+1) x m; Y m x d (real
+    basis, a complex pair as real and imaginary parts), theta d complex."""
+    H = np.ascontiguousarray(Hbar, dtype=np.float64)
+    m = H.shape[1]
+    if H.shape != (m + 1, m):
+        raise ValueError("Hbar must be (m+1) x m")
+    Y = np.empty((m, d))
+    tr = np.empty(d)
+    ti = np.empty(d)
+    _check(load().sld_harmonic_ritz(H.ctypes.data, m, int(d), Y.ctypes.data, tr.ctypes.data, ti.ctypes.data))
+    return Y, tr + 1j * ti
 
 
 def from_problem(P, stream=None) -> System:
