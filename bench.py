@@ -157,7 +157,8 @@ def gmres_bytes(n, m, its, cycles, deflated):
 def bench_gmres(sld, torch, s, x, P, m=20, tol=1e-6):
     """PDGMRES(m) (the paper's solver: deflated right-Jacobi GMRES, FP64) on
     the bench workload at the paper's tolerance, against plain GMRES(m)
-    (capped) and deflated CG to the same tolerance."""
+    (capped) and deflated CG to the same tolerance; and RDGMRES(30, 3)
+    (harmonic-Ritz deflation) against plain GMRES(30), both capped."""
     out = {"m": m, "tol": tol, "precision": "fp64"}
     for name, defl, cap in (("deflated", True, 20000), ("plain", False, 2000)):
         s.solve_gmres(x=x, m=m, deflate=defl, tol=tol, maxiter=min(cap, 50), raise_on_error=False)  # warm-up
@@ -169,6 +170,16 @@ def bench_gmres(sld, torch, s, x, P, m=20, tol=1e-6):
                      "alg_gbs": by / (g.solve_ms * 1e-3) / 1e9}
     _, c = s.solve(x=x, precision=sld.FP64, tol=tol)
     out["dpcg_fp64_same_tol"] = {"iterations": c.iterations, "ms": c.solve_ms}
+    # harmonic-Ritz deflation (RDGMRES(30, 3)) against plain GMRES(30), both capped
+    try:
+        _, r30 = s.solve_rdgmres(x=x, m=30, d=3, tol=tol, maxiter=4000, raise_on_error=False)
+        _, g30 = s.solve_gmres(x=x, m=30, deflate=False, tol=tol, maxiter=4000, raise_on_error=False)
+        out["rdgmres_m30_d3"] = {"iterations": r30.iterations, "ms": r30.solve_ms, "converged": r30.status == 0,
+                                 "true_relres": r30.true_relres}
+        out["gmres_m30_plain"] = {"iterations": g30.iterations, "ms": g30.solve_ms, "converged": g30.status == 0,
+                                  "true_relres": g30.true_relres}
+    except Exception as ex:  # reported, not fatal to the line
+        out["rdgmres_m30_d3"] = {"error": str(ex)}
     return out
 
 

@@ -239,6 +239,25 @@ sld_status sld_solve_gmres(sld_system s, const double* b, int m, int deflate, do
                            double* x, sld_gmres_info* info);
 
 /*
+ * RDGMRES: restarted GMRES(m) with harmonic-Ritz deflation (Section 3.2.1 and
+ * its algorithm).  The first cycle is plain right-preconditioned GMRES(m)
+ * (M = diag A) in the preconditioned variable u (x = M^{-1} u); its d
+ * harmonic Ritz vectors of smallest |theta| (sld_harmonic_ritz) give
+ * Z = V_m Y, and with B = A M^{-1}, E = Z^T B Z, P1 = I - B Z E^{-1} Z^T,
+ * P2 = I - Z E^{-1} Z^T B the remaining cycles solve P1 B t = P1 r1
+ * (r1 = b - B u1); x = M^{-1} (u1 + P2 t + Z E^{-1} Z^T r1).  FP64; the
+ * kernels of sld_solve_gmres.  Needs no label deflation.
+ *   b: n values (host or device) or NULL (the assembled rhs).  2 <= m <= 31,
+ *   1 <= d <= min(8, m), tol in (0, 1), maxiter >= 1.  x: n values (output).
+ * Work space: (m + 2 d + 7) n FP64 on the device, per call.
+ * Errors: SLD_ERR_INVALID_ARG, SLD_ERR_OOM, SLD_ERR_CUDA, SLD_ERR_BREAKDOWN
+ * (harmonic Ritz pairs), SLD_ERR_COARSE_SINGULAR (E singular),
+ * SLD_ERR_NOT_CONVERGED (x and info still written).
+ */
+sld_status sld_solve_rdgmres(sld_system s, const double* b, int m, int d, double tol, int maxiter, double* x,
+                             sld_gmres_info* info);
+
+/*
  * Harmonic Ritz pairs of an Arnoldi cycle (host computation; Section 3.2.1,
  * eq. (defleig) form (a)): with the (m+1) x m Hessenberg matrix Hbar of m
  * Arnoldi steps, F = H_m + h_{m+1,m}^2 H_m^{-T} e_m e_m^T, F y = theta y;

@@ -517,6 +517,47 @@ sld_status sld_solve_gmres(sld_system s, const double* b, int m, int deflate, do
   return SLD_OK;
 }
 
+sld_status sld_solve_rdgmres(sld_system s, const double* b, int m, int d, double tol, int maxiter, double* x,
+                             sld_gmres_info* info) {
+  g_last_error.clear();
+  if (!s) return fail(SLD_ERR_INVALID_ARG, "handle is NULL");
+  if (!x) return fail(SLD_ERR_INVALID_ARG, "x is NULL");
+  if (m < 2 || m > 31) return fail(SLD_ERR_INVALID_ARG, "m must be in 2 .. 31");
+  if (d < 1 || d > 8 || d > m) return fail(SLD_ERR_INVALID_ARG, "d must be in 1 .. min(8, m)");
+  if (!(tol > 0) || !(tol < 1)) return fail(SLD_ERR_INVALID_ARG, "tol must be in (0, 1)");
+  if (maxiter < 1) return fail(SLD_ERR_INVALID_ARG, "maxiter must be >= 1");
+  sld_status st = ensure_workspace(s, false, false);
+  if (st != SLD_OK) return st;
+  const int64_t n = s->g.n;
+  const double* bd = s->b;
+  cudaError_t e;
+  if (b) {
+    if (is_device_ptr(b)) {
+      bd = b;
+    } else {
+      if ((e = cudaMemcpyAsync(s->bwork, b, sizeof(double) * n, cudaMemcpyHostToDevice, s->stream)) != cudaSuccess)
+        return cuda_fail(e, "copy b");
+      bd = s->bwork;
+    }
+  }
+  sld_gmres_info r{};
+  std::string msg;
+  const int code = sld::run_rdgmres(s, bd, m, d, tol, maxiter, &r, &msg);
+  if (code != SLD_OK && code != SLD_ERR_NOT_CONVERGED) {
+    if (info) *info = r;
+    return fail((sld_status)code, msg);
+  }
+  double rr = 0, bb = 0;
+  if ((e = sld::launch_residual(s, bd, s->x, s->part, &rr, &bb)) != cudaSuccess) return cuda_fail(e, "residual");
+  r.true_relres = bb > 0 ? std::sqrt(rr / bb) : 0.0;
+  if ((e = cudaMemcpyAsync(x, s->x, sizeof(double) * n, kind_out(x), s->stream)) != cudaSuccess)
+    return cuda_fail(e, "copy x out");
+  if ((e = cudaStreamSynchronize(s->stream)) != cudaSuccess) return cuda_fail(e, "copy x out");
+  if (info) *info = r;
+  if (code != SLD_OK) return fail((sld_status)code, msg);
+  return SLD_OK;
+}
+
 void sld_destroy(sld_system s) {
   if (!s) return;
   if (s->stream) cudaStreamSynchronize(s->stream);

@@ -37,12 +37,13 @@ constexpr int kGT = 256;         // threads per CTA
 constexpr int kGMaxBasis = 32;   // basis vectors (m + 1)
 constexpr int kGDots = 8;        // basis vectors per CTA in k_gm_dots
 
-enum { GM_PRECOND = 0, GM_RESID = 1, GM_APPLY = 2, GM_COPY = 3 };
+enum { GM_PRECOND = 0, GM_RESID = 1, GM_APPLY = 2, GM_COPY = 3, GM_BAPPLY = 4 };
 
 // w = op(v) at every cell, and this CTA's row of Z^T w.
 //   GM_PRECOND: v is the raw next basis vector; v_j = v / sqrt(*norm2) is
 //               written to vout and w = A M^{-1} v_j
 //   GM_RESID:   w = b - A v        GM_APPLY: w = A v        GM_COPY: w = v (not stored)
+//   GM_BAPPLY:  w = A M^{-1} v (the right-preconditioned operator B)
 template <int MODE, bool WACC>
 __global__ void __launch_bounds__(kGT) k_gm_apply(SolveArgs a, const double* __restrict__ v,
                                                   const double* __restrict__ norm2, double* __restrict__ vout,
@@ -73,6 +74,8 @@ __global__ void __launch_bounds__(kGT) k_gm_apply(SolveArgs a, const double* __r
       wv = a.b[i] - apply64(a, cw, [&](int64_t j, int64_t) { return v[j]; });
     } else if constexpr (MODE == GM_APPLY) {
       wv = apply64(a, cw, [&](int64_t j, int64_t) { return v[j]; });
+    } else if constexpr (MODE == GM_BAPPLY) {
+      wv = apply64(a, cw, [&](int64_t j, int64_t) { return v[j] * a.invdiag64[j]; });
     } else {
       wv = v[i];
     }
@@ -221,6 +224,13 @@ __global__ void __launch_bounds__(kGT) k_gm_update(int64_t n, const double* __re
     for (int k = 0; k < nv; ++k) t += us[k] * V[(int64_t)k * n + i];
     xt[i] += invdiag[i] * t;
   }
+}
+
+// x = M^{-1} (u1 + delta)
+__global__ void k_rd_final(int64_t n, const double* __restrict__ invdiag, const double* __restrict__ u1,
+                           const double* __restrict__ delta, double* __restrict__ x) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[i] = invdiag[i] * (u1[i] + delta[i]);
 }
 
 // x = x~ - Z y1 + Z y0   (P2 x~ + x*, y1 = E^{-1} Z^T A x~, y0 = E^{-1} Z^T b)
@@ -454,6 +464,276 @@ int run_gmres(sld_system s, const double* b, int m, int deflate, double tol, int
   info->solve_ms = ms;
   if (!converged) {
     *msg = "GMRES did not reach the tolerance within maxiter steps";
+    return SLD_ERR_NOT_CONVERGED;
+  }
+  return SLD_OK;
+}
+
+// RDGMRES (Section 3.2.1): the first cycle is plain right-preconditioned
+// GMRES(m) in the preconditioned variable u (x = M^{-1} u, B = A M^{-1});
+// from its Arnoldi data the d harmonic Ritz vectors of smallest |theta|
+// (harmonic_ritz) give Z = V_m Y; with E = Z^T B Z, P1 = I - B Z E^{-1} Z^T
+// and P2 = I - Z E^{-1} Z^T B, the correction delta (B delta = r1 = b - B u1)
+// is P2 t + Z E^{-1} Z^T r1 with t from GMRES(m) on P1 B t = P1 r1, and
+// x = M^{-1} (u1 + delta).  b - A x = P1 (r1 - B t): the GMRES residual is
+// the residual of x.  The kernels are PDGMRES's, with no label columns.
+int run_rdgmres(sld_system s, const double* b, int m, int nd, double tol, int maxiter, sld_gmres_info* info,
+                std::string* msg) {
+  const int64_t n = s->g.n;
+  cudaStream_t st = s->stream;
+  sld_options o;
+  sld_default_options(&o);
+  o.precision = SLD_FP64;
+  SolveArgs a;
+  fill_args(s, b, o, &a);
+  a.d = 0;
+  a.dk = 0;
+  a.kL = 0;
+  const int G = std::min(s->nsm * 4, s->part_rows);
+  a.sy.ncta = G;
+  a.sy.cta0 = 0;
+  const int ps = a.pstride;
+  double* part = a.part;
+  // device: basis V (m+1) n; Z, BZ (nd n each); w, raw, u1, r1, t, tmp (n each); small
+  double *V = nullptr, *work = nullptr;
+  Scal* sc = nullptr;
+  const size_t nsmall = (size_t)nd * nd + 3 * (size_t)nd + 2 * (size_t)kGMaxBasis + 8;
+  auto release = [&]() {
+    cudaFree(V);
+    cudaFree(work);
+    cudaFree(sc);
+  };
+  cudaError_t e = cudaMalloc(&V, sizeof(double) * (size_t)(m + 1) * n);
+  if (e == cudaSuccess) e = cudaMalloc(&work, sizeof(double) * ((size_t)(2 * nd + 6) * n + nsmall));
+  if (e == cudaSuccess) e = cudaMalloc(&sc, sizeof(Scal));
+  if (e != cudaSuccess) {
+    release();
+    *msg = std::string("RDGMRES work space: ") + cudaGetErrorString(e);
+    return SLD_ERR_OOM;
+  }
+  double *Z = work, *BZ = Z + (size_t)nd * n, *w = BZ + (size_t)nd * n, *raw = w + n, *u1 = raw + n, *r1 = u1 + n,
+         *t = r1 + n, *tmp = t + n;
+  double *Einv = tmp + n, *sv = Einv + (size_t)nd * nd, *cv = sv + nd, *one = cv + nd, *coef = one + nd;
+  const size_t smem = sizeof(double);  // no label sums
+  auto cols = [&](int ncol) { return dim3((unsigned)((ncol + 7) / 8)); };
+  auto colsum = [&](int ncol, double* out) { k_gm_colsum<<<cols(ncol), 256, 0, st>>>(part, ps, G, ncol, out); };
+  auto Bapply = [&](const double* v, double* out) {
+    k_gm_apply<GM_BAPPLY, true><<<G, kGT, smem, st>>>(a, v, nullptr, nullptr, out, part);
+  };
+  auto precond = [&](const double* rawv, double* vj, double* out) {
+    k_gm_apply<GM_PRECOND, true><<<G, kGT, smem, st>>>(a, rawv, &sc->nn, vj, out, part);
+  };
+  auto dots_of = [&](const double* basis, int nv, const double* vec, double* out) {
+    k_gm_dots<<<dim3(G, (nv + kGDots - 1) / kGDots), kGT, 0, st>>>(n, basis, nv, vec, part, ps);
+    colsum(nv, out);
+  };
+  // out = vec - sum_k h_k basis_k (|out|^2 into sc->nn when want_norm)
+  auto minus_comb = [&](const double* basis, int nv, const double* h, const double* vec, double* out,
+                        bool want_norm) {
+    k_gm_orth<<<G, kGT, 0, st>>>(n, basis, nv, h, vec, out, part, ps, want_norm ? 0 : -1);
+    if (want_norm) colsum(1, &sc->nn);
+  };
+  Scal hs;
+  auto fetch = [&]() -> bool {
+    if ((e = cudaMemcpyAsync(&hs, sc, sizeof(Scal), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return false;
+    return (e = cudaStreamSynchronize(st)) == cudaSuccess;
+  };
+  auto fail_cuda = [&]() {
+    release();
+    *msg = std::string("RDGMRES: ") + cudaGetErrorString(e);
+    return (int)SLD_ERR_CUDA;
+  };
+  // host-side GMRES(m) cycle state
+  std::vector<double> R((size_t)(m + 1) * m), Hb((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), u(m);
+  int its = 0, cycles = 0;
+  double est = 0.0;
+  cudaEventRecord(s->ev0, st);
+  // ||b||; raw = b, sc->nn = ||b||^2
+  minus_comb(V, 0, sc->h1, b, raw, true);
+  if (!fetch()) return fail_cuda();
+  const double bnorm = std::sqrt(hs.nn);
+  {
+    const double h1 = 1.0;
+    cudaMemcpyAsync(one, &h1, sizeof(double), cudaMemcpyHostToDevice, st);
+  }
+  cudaMemsetAsync(u1, 0, sizeof(double) * n, st);
+  cudaMemsetAsync(t, 0, sizeof(double) * n, st);
+  // One GMRES(m) cycle from raw (|raw|^2 in sc->nn); `deflated` applies P1
+  // after B.  The solution of the least-squares problem is added to `acc`.
+  // Returns the steps taken, or -1 on a CUDA error.
+  bool converged = bnorm == 0.0;
+  auto cycle = [&](bool deflated, double* acc) -> int {
+    const double beta = std::sqrt(hs.nn);
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int k = 0;
+    for (int j = 0; j < m; ++j) {
+      precond(raw, V + (size_t)j * n, w);  // v_j = raw / |raw|, w = B v_j
+      if (deflated) {                      // w -= B Z E^{-1} Z^T w
+        dots_of(Z, nd, w, sv);
+        k_gm_gemv<<<cols(nd), 256, 0, st>>>(nd, Einv, sv, cv);
+        minus_comb(BZ, nd, cv, w, w, false);
+      }
+      dots_of(V, j + 1, w, sc->h1);
+      minus_comb(V, j + 1, sc->h1, w, w, false);
+      dots_of(V, j + 1, w, sc->h2);
+      minus_comb(V, j + 1, sc->h2, w, raw, true);
+      if (!fetch()) return -1;
+      std::vector<double> col(j + 2);
+      for (int i = 0; i <= j; ++i) col[i] = Hb[(size_t)i * m + j] = hs.h1[i] + hs.h2[i];
+      const double hn = std::sqrt(hs.nn);
+      col[j + 1] = Hb[(size_t)(j + 1) * m + j] = hn;
+      for (int i = 0; i < j; ++i) {
+        const double tt = cs[i] * col[i] + sn[i] * col[i + 1];
+        col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+        col[i] = tt;
+      }
+      const double rho = std::hypot(col[j], col[j + 1]);
+      cs[j] = rho == 0.0 ? 1.0 : col[j] / rho;
+      sn[j] = rho == 0.0 ? 0.0 : col[j + 1] / rho;
+      col[j] = rho;
+      col[j + 1] = 0.0;
+      for (int i = 0; i <= j + 1; ++i) R[(size_t)i * m + j] = col[i];
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      ++its;
+      k = j + 1;
+      est = std::fabs(g[j + 1]) / bnorm;
+      if (std::fabs(g[j + 1]) <= tol * bnorm || hn == 0.0 || its >= maxiter) break;
+    }
+    for (int i = k - 1; i >= 0; --i) {
+      double tt = g[i];
+      for (int q = i + 1; q < k; ++q) tt -= R[(size_t)i * m + q] * u[q];
+      u[i] = R[(size_t)i * m + i] != 0.0 ? tt / R[(size_t)i * m + i] : 0.0;
+    }
+    for (int i = 0; i < k; ++i) u[i] = -u[i];  // acc -= sum (-u_i) V_i
+    cudaMemcpyAsync(coef, u.data(), sizeof(double) * k, cudaMemcpyHostToDevice, st);
+    minus_comb(V, k, coef, acc, acc, false);
+    ++cycles;
+    return k;
+  };
+  int k1 = 0;
+  if (!converged) {
+    k1 = cycle(false, u1);
+    if (k1 < 0) return fail_cuda();
+  }
+  // residual after the first cycle: r1 = b - B u1
+  Bapply(u1, w);
+  minus_comb(w, 1, one, b, r1, true);
+  if (!fetch()) return fail_cuda();
+  est = bnorm > 0 ? std::sqrt(hs.nn) / bnorm : 0.0;
+  if (!converged && std::sqrt(hs.nn) > tol * bnorm && its < maxiter && k1 == m) {
+    // harmonic Ritz vectors of the first cycle: Z = V_m Y, BZ = B Z, E = Z^T B Z
+    std::vector<double> Y((size_t)m * nd), tr(nd), ti(nd);
+    if (harmonic_ritz(Hb.data(), m, nd, Y.data(), tr.data(), ti.data()) != SLD_OK) {
+      release();
+      *msg = "RDGMRES: harmonic Ritz pairs failed";
+      return SLD_ERR_BREAKDOWN;
+    }
+    std::vector<double> ycol(m);
+    for (int kz = 0; kz < nd; ++kz) {
+      for (int j = 0; j < m; ++j) ycol[j] = -Y[(size_t)j * nd + kz];
+      cudaMemcpyAsync(coef, ycol.data(), sizeof(double) * m, cudaMemcpyHostToDevice, st);
+      cudaMemsetAsync(Z + (size_t)kz * n, 0, sizeof(double) * n, st);
+      minus_comb(V, m, coef, Z + (size_t)kz * n, Z + (size_t)kz * n, false);
+      if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail_cuda();  // coef is reused
+      Bapply(Z + (size_t)kz * n, BZ + (size_t)kz * n);
+    }
+    std::vector<double> E((size_t)nd * nd), col(nd);
+    for (int kz = 0; kz < nd; ++kz) {
+      dots_of(Z, nd, BZ + (size_t)kz * n, sv);  // column kz: Z_i . B Z_kz
+      if ((e = cudaMemcpyAsync(col.data(), sv, sizeof(double) * nd, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+          (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return fail_cuda();
+      for (int i = 0; i < nd; ++i) E[(size_t)i * nd + kz] = col[i];
+    }
+    // E^{-1} by Gauss-Jordan with partial pivoting
+    std::vector<double> Mx = E, Inv((size_t)nd * nd, 0.0);
+    for (int i = 0; i < nd; ++i) Inv[(size_t)i * nd + i] = 1.0;
+    double emax = 0.0;
+    for (double vv : E) emax = std::max(emax, std::fabs(vv));
+    for (int c = 0; c < nd; ++c) {
+      int p = c;
+      for (int r = c + 1; r < nd; ++r)
+        if (std::fabs(Mx[(size_t)r * nd + c]) > std::fabs(Mx[(size_t)p * nd + c])) p = r;
+      if (!(std::fabs(Mx[(size_t)p * nd + c]) > 1e-14 * emax)) {
+        release();
+        *msg = "RDGMRES: the coarse matrix of the harmonic Ritz vectors is singular";
+        return SLD_ERR_COARSE_SINGULAR;
+      }
+      for (int j = 0; j < nd; ++j) {
+        std::swap(Mx[(size_t)c * nd + j], Mx[(size_t)p * nd + j]);
+        std::swap(Inv[(size_t)c * nd + j], Inv[(size_t)p * nd + j]);
+      }
+      const double piv = Mx[(size_t)c * nd + c];
+      for (int j = 0; j < nd; ++j) {
+        Mx[(size_t)c * nd + j] /= piv;
+        Inv[(size_t)c * nd + j] /= piv;
+      }
+      for (int r = 0; r < nd; ++r) {
+        if (r == c) continue;
+        const double f = Mx[(size_t)r * nd + c];
+        for (int j = 0; j < nd; ++j) {
+          Mx[(size_t)r * nd + j] -= f * Mx[(size_t)c * nd + j];
+          Inv[(size_t)r * nd + j] -= f * Inv[(size_t)c * nd + j];
+        }
+      }
+    }
+    cudaMemcpyAsync(Einv, Inv.data(), sizeof(double) * nd * nd, cudaMemcpyHostToDevice, st);
+    // deflated cycles on P1 B t = P1 r1
+    for (;;) {
+      // raw = P1 (r1 - B t), |raw|^2
+      Bapply(t, w);
+      minus_comb(w, 1, one, r1, tmp, false);
+      dots_of(Z, nd, tmp, sv);
+      k_gm_gemv<<<cols(nd), 256, 0, st>>>(nd, Einv, sv, cv);
+      minus_comb(BZ, nd, cv, tmp, raw, true);
+      if (!fetch()) return fail_cuda();
+      est = std::sqrt(hs.nn) / bnorm;
+      if (std::sqrt(hs.nn) <= tol * bnorm) {
+        converged = true;
+        break;
+      }
+      if (its >= maxiter) break;
+      if (cycle(true, t) < 0) return fail_cuda();
+    }
+    // delta = t + Z E^{-1} Z^T (r1 - B t); x = M^{-1} (u1 + delta)
+    Bapply(t, w);
+    minus_comb(w, 1, one, r1, tmp, false);
+    dots_of(Z, nd, tmp, sv);
+    k_gm_gemv<<<cols(nd), 256, 0, st>>>(nd, Einv, sv, cv);
+    // tmp = t + Z cv: negate cv on the device side by combining with -1
+    {
+      std::vector<double> c_h(nd);
+      if ((e = cudaMemcpyAsync(c_h.data(), cv, sizeof(double) * nd, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+          (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return fail_cuda();
+      for (double& vv : c_h) vv = -vv;
+      cudaMemcpyAsync(coef, c_h.data(), sizeof(double) * nd, cudaMemcpyHostToDevice, st);
+    }
+    minus_comb(Z, nd, coef, t, tmp, false);
+    k_rd_final<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, a.invdiag64, u1, tmp, a.x);
+  } else {
+    converged = converged || std::sqrt(hs.nn) <= tol * bnorm;
+    cudaMemsetAsync(tmp, 0, sizeof(double) * n, st);
+    k_rd_final<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, a.invdiag64, u1, tmp, a.x);
+  }
+  cudaEventRecord(s->ev1, st);
+  e = cudaEventSynchronize(s->ev1);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  float ms = 0.0f;
+  cudaEventElapsedTime(&ms, s->ev0, s->ev1);
+  release();
+  if (e != cudaSuccess) {
+    *msg = std::string("RDGMRES: ") + cudaGetErrorString(e);
+    return SLD_ERR_CUDA;
+  }
+  info->iterations = its;
+  info->cycles = cycles;
+  info->relres_estimate = est;
+  info->solve_ms = ms;
+  if (!converged) {
+    *msg = "RDGMRES did not reach the tolerance within maxiter steps";
     return SLD_ERR_NOT_CONVERGED;
   }
   return SLD_OK;

@@ -177,6 +177,9 @@ int harmonic_ritz(const double* Hbar, int m, int d, double* Y, double* theta_re,
 // b: device.  Writes the solution to s->x.  Returns an sld_status.
 int run_gmres(sld_system s, const double* b, int m, int deflate, double tol, int maxiter, sld_gmres_info* info,
               std::string* msg);
+// RDGMRES (harmonic-Ritz deflation from the first cycle, nd vectors); b: device
+int run_rdgmres(sld_system s, const double* b, int m, int nd, double tol, int maxiter, sld_gmres_info* info,
+                std::string* msg);
 // sld_solve.cu
 void fill_args(sld_system s, const double* b_dev, const sld_options& o, SolveArgs* a);
 int run_solve(sld_system s, const double* b_dev, const sld_options& o, sld_result* res,

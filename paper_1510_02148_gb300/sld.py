@@ -34,7 +34,7 @@ EXPORTED = ["sld_default_options", "sld_build_system", "sld_make_labels", "sld_b
             "sld_net_num_params", "sld_net_create", "sld_net_set_params", "sld_net_get_params",
             "sld_net_get_grads", "sld_net_forward", "sld_net_backward", "sld_net_loss_backward",
             "sld_net_adam", "sld_net_destroy", "sld_lanczos_eigvecs", "sld_solve_gmres",
-            "sld_make_labels_cc", "sld_harmonic_ritz"]
+            "sld_make_labels_cc", "sld_harmonic_ritz", "sld_solve_rdgmres"]
 
 
 class SldError(RuntimeError):
@@ -116,6 +116,7 @@ def load(path: str = LIB_PATH):
         lib.sld_net_destroy.restype = None
         lib.sld_lanczos_eigvecs.argtypes = [P, C.c_int, C.c_int, P, P, P]
         lib.sld_make_labels_cc.argtypes = [P, C.c_int, C.c_int, C.c_int, P, C.c_int, P, C.POINTER(C.c_int)]
+        lib.sld_solve_rdgmres.argtypes = [P, P, C.c_int, C.c_int, C.c_double, C.c_int, P, C.POINTER(GmresInfo)]
         lib.sld_harmonic_ritz.argtypes = [P, C.c_int, C.c_int, P, P, P]
         lib.sld_solve_gmres.argtypes = [P, P, C.c_int, C.c_int, C.c_double, C.c_int, P, C.POINTER(GmresInfo)]
         for name in ("sld_build_system", "sld_make_labels", "sld_build_deflation", "sld_solve",
@@ -278,6 +279,19 @@ class System:
         r = GmresInfo()
         st = load().sld_solve_gmres(self._h, _ptr(b, np.float64), int(m), 1 if deflate else 0, float(tol),
                                     int(maxiter), _ptr(x, np.float64), C.byref(r))
+        r.status = st
+        if st != OK and raise_on_error:
+            _check(st)
+        return x, r
+
+    def solve_rdgmres(self, b=None, x=None, m=30, d=3, tol=1e-6, maxiter=5000, raise_on_error=True):
+        """RDGMRES (sld_solve_rdgmres): GMRES(m) deflated with the d harmonic
+        Ritz vectors of its first cycle, FP64.  Returns (x, GmresInfo)."""
+        if x is None:
+            x = np.empty(self.n, dtype=np.float64)
+        r = GmresInfo()
+        st = load().sld_solve_rdgmres(self._h, _ptr(b, np.float64), int(m), int(d), float(tol), int(maxiter),
+                                      _ptr(x, np.float64), C.byref(r))
         r.status = st
         if st != OK and raise_on_error:
             _check(st)
