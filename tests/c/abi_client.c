@@ -31,6 +31,16 @@ int main(void) {
   CHECK(sld_solve_gmres(NULL, NULL, 20, 1, 1e-6, 100, &x, NULL) == SLD_ERR_INVALID_ARG);
   int d = -1;
   CHECK(sld_make_labels_cc(NULL, 1, 1, 1, NULL, 1, NULL, &d) == SLD_ERR_INVALID_ARG);
+  CHECK(sld_solve_rdgmres(NULL, NULL, 30, 3, 1e-6, 100, &x, NULL) == SLD_ERR_INVALID_ARG);
+  {
+    /* harmonic Ritz pairs of a 2-step "Arnoldi cycle": pure host code */
+    const double Hbar[3 * 2] = {2.0, 1.0, 1.0, 3.0, 0.0, 0.0}; /* h_{3,2} = 0: F = H_2 */
+    double Y[2 * 2], tre[2], tim[2];
+    CHECK(sld_harmonic_ritz(Hbar, 2, 2, Y, tre, tim) == SLD_OK);
+    /* eigenvalues of [[2, 1], [1, 3]]: (5 -+ sqrt 5) / 2, smallest first */
+    CHECK(tre[0] > 1.38 && tre[0] < 1.39 && tre[1] > 3.61 && tre[1] < 3.62 && tim[0] == 0.0);
+    CHECK(sld_harmonic_ritz(Hbar, 1, 1, Y, tre, tim) == SLD_ERR_INVALID_ARG);
+  }
   CHECK(sld_net_num_params() > 0);
   sld_destroy(NULL); /* ignored */
   printf("%s\n", fails ? "FAIL" : "OK");
