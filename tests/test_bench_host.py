@@ -1,0 +1,65 @@
+"""Host-side arithmetic of the benchmark line (no GPU): the PDGMRES byte
+count against a step-by-step tally of its passes, the clock-record parser
+and the peak lookup."""
+import json
+import os
+
+import pytest
+
+import bench
+
+
+def _tally(n, m, its, deflated):
+    """Step by step: a cycle's residual pass, then per Arnoldi step with basis
+    size j+1 the apply, the deflation, two dot and two orthogonalisation
+    passes over the basis."""
+    tot, left = 0, its
+    while left > 0:
+        k = min(m, left)
+        left -= k
+        tot += (68 + 52 + 16) if deflated else (68 + 16 - 4)
+        for j in range(k):
+            dot = (j + 1) * 8 + 8     # basis and w read
+            orth = (j + 1) * 8 + 16   # basis read, w read and written
+            step = 68 + 2 * dot + 2 * orth
+            if deflated:
+                step += 52
+            else:
+                step -= 4  # no label read in the apply
+            tot += step
+    return n * tot
+
+
+@pytest.mark.parametrize("deflated", [False, True])
+@pytest.mark.parametrize("m,its", [(20, 20), (20, 47), (5, 1), (30, 90)])
+def test_gmres_bytes_matches_step_tally(deflated, m, its):
+    cycles = -(-its // m)
+    assert bench.gmres_bytes(1000, m, its, cycles, deflated) == _tally(1000, m, its, deflated)
+
+
+def test_clock_summary_parses_nvidia_smi_lines():
+    c = bench.ClockSampler()
+    c.lines = [
+        "0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "0, 2055, 2070, 1100.4, 0x4, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 1200.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "garbage",
+        "0, [N/A], 2070, 1.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+    ]
+    s = c.summary()
+    assert s["sm_mhz"] == 2070 and s["sm_max_mhz"] == 2070
+    assert s["reasons"] == ["sw_power_cap"] and s["samples"] == 3
+
+
+def test_clock_summary_empty():
+    s = bench.ClockSampler().summary()
+    assert s["sm_mhz"] is None and s["samples"] == 0 and s["reasons"] == []
+
+
+def test_peaks_from_measured_file():
+    p = os.path.join(bench.ROOT, "MEASURED_PEAKS.json")
+    val, kind = bench._peaks()
+    if os.path.exists(p):
+        assert kind == "measured" and val == float(json.load(open(p))["hbm_gbs"])
+    else:
+        assert (val, kind) == (6800.0, "fallback")
