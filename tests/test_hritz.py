@@ -82,3 +82,40 @@ def test_same_space_as_the_oracle_on_arnoldi_data(lib):
 def test_argument_errors(lib):
     with pytest.raises(lib.SldError, match="INVALID_ARG"):
         lib.harmonic_ritz(np.zeros((2, 1)), 1)
+
+
+def test_all_pairs_span_the_whole_space(lib):
+    """d = m: every eigenvalue of F once (a conjugate pair as two values) and
+    a basis of the whole space."""
+    rng = np.random.default_rng(11)
+    m = 9
+    H = np.triu(rng.standard_normal((m + 1, m)), -1)
+    Y, theta = lib.harmonic_ritz(H, m)
+    ev = np.linalg.eigvals(_F(H))
+    np.testing.assert_allclose(np.sort_complex(theta), np.sort_complex(ev), rtol=1e-8, atol=1e-12)
+    assert np.linalg.matrix_rank(Y, tol=1e-8 * np.linalg.norm(Y)) == m
+
+
+def test_largest_cycle(lib):
+    rng = np.random.default_rng(12)
+    m = 64
+    H = np.triu(rng.standard_normal((m + 1, m)), -1) + 4.0 * np.eye(m + 1, m)
+    Y, theta = lib.harmonic_ritz(H, 5)
+    ev = np.linalg.eigvals(_F(H))
+    np.testing.assert_allclose(np.sort(np.abs(theta)), np.sort(np.abs(ev))[:5], rtol=1e-8)
+
+
+def test_singular_and_non_finite_hessenberg(lib):
+    m = 5
+    H = np.triu(np.ones((m + 1, m)), -1)
+    H[:, 2] = 0.0   # H_m singular while h_{m+1,m} != 0: F is undefined
+    with pytest.raises(lib.SldError, match="BREAKDOWN"):
+        lib.harmonic_ritz(H, 2)
+    H = np.triu(np.ones((m + 1, m)), -1) + np.eye(m + 1, m)
+    H[1, 3] = np.nan
+    with pytest.raises(lib.SldError):
+        lib.harmonic_ritz(H, 2)
+    with pytest.raises(lib.SldError, match="INVALID_ARG"):
+        lib.harmonic_ritz(np.triu(np.ones((66, 65)), -1), 2)
+    with pytest.raises(lib.SldError, match="INVALID_ARG"):
+        lib.harmonic_ritz(np.triu(np.ones((5, 4)), -1), 5)
