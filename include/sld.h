@@ -359,7 +359,9 @@ sld_status sld_get_coarse(sld_system s, double* E, double* Einv);
  * device.
  *   v: n values in device memory; out: d values in device memory (host
  *   pointers are rejected: staging them would need a buffer).  d <= 1024.
- *   The handle's device must be the current device.
+ *   The handle's device must be the current device, and v and out must be
+ *   memory of that same GPU (or managed memory): device memory of another
+ *   GPU is rejected, since the kernels would read it directly.
  * Work runs on the handle's stream and is asynchronous: out is valid once
  * that stream has reached the call.  The partial sums go to a fixed 1 MiB
  * __device__ array (128 CTAs x 1024 labels) that every GPU loading the
@@ -368,8 +370,8 @@ sld_status sld_get_coarse(sld_system s, double* E, double* Einv);
  * current; make that first call before any stream capture.  Every call
  * shares the array and overwrites what it reads, so calls whose kernels
  * overlap on the GPU (other streams, other host threads) race.
- * Errors: SLD_ERR_INVALID_ARG (d > 1024, host pointer, wrong current
- * device), SLD_ERR_STATE (no deflation built), SLD_ERR_CUDA.
+ * Errors: SLD_ERR_INVALID_ARG (d > 1024, host pointer, another GPU's
+ * memory, wrong current device), SLD_ERR_STATE (no deflation built), SLD_ERR_CUDA.
  */
 sld_status sld_restrict_noalloc(sld_system s, const double* v, double* out);
 

@@ -85,30 +85,32 @@ bool hessenberg_eigenvalues(std::vector<double>& a, int n, std::vector<cd>* ev) 
     double z = A(l + 1, l) * A(l + 2, l + 1);
     for (int k = l; k <= hi - 2; ++k) {
       // Householder reflector P = I - 2 v v^T / v^T v with P (x, y, z)^T = (alpha, 0, 0)^T
+      // A zero (x, y, z) needs no reflector; the bulge chase still moves on
+      // to the next column, so the reload below runs on every k.
       const double nrm = std::sqrt(x * x + y * y + z * z);
-      if (nrm == 0.0) continue;
       const double alpha = x > 0.0 ? -nrm : nrm;
-      double v0 = x - alpha, v1 = y, v2 = z;
+      const double v0 = x - alpha, v1 = y, v2 = z;
       const double vv = v0 * v0 + v1 * v1 + v2 * v2;
-      if (vv == 0.0) continue;
-      const double f = 2.0 / vv;
-      const int c0 = std::max(l, k - 1);
-      for (int j = c0; j < n; ++j) {  // rows k .. k+2 from the left
-        const double dot = v0 * A(k, j) + v1 * A(k + 1, j) + v2 * A(k + 2, j);
-        A(k, j) -= f * v0 * dot;
-        A(k + 1, j) -= f * v1 * dot;
-        A(k + 2, j) -= f * v2 * dot;
-      }
-      const int r1 = std::min(hi, k + 3);
-      for (int i = 0; i <= r1; ++i) {  // columns k .. k+2 from the right
-        const double dot = v0 * A(i, k) + v1 * A(i, k + 1) + v2 * A(i, k + 2);
-        A(i, k) -= f * v0 * dot;
-        A(i, k + 1) -= f * v1 * dot;
-        A(i, k + 2) -= f * v2 * dot;
+      if (nrm != 0.0 && vv != 0.0) {
+        const double f = 2.0 / vv;
+        const int c0 = std::max(l, k - 1);
+        for (int j = c0; j < n; ++j) {  // rows k .. k+2 from the left
+          const double dot = v0 * A(k, j) + v1 * A(k + 1, j) + v2 * A(k + 2, j);
+          A(k, j) -= f * v0 * dot;
+          A(k + 1, j) -= f * v1 * dot;
+          A(k + 2, j) -= f * v2 * dot;
+        }
+        const int r1 = std::min(hi, k + 3);
+        for (int i = 0; i <= r1; ++i) {  // columns k .. k+2 from the right
+          const double dot = v0 * A(i, k) + v1 * A(i, k + 1) + v2 * A(i, k + 2);
+          A(i, k) -= f * v0 * dot;
+          A(i, k + 1) -= f * v1 * dot;
+          A(i, k + 2) -= f * v2 * dot;
+        }
       }
       x = A(k + 1, k);
       y = A(k + 2, k);
-      if (k < hi - 2) z = A(k + 3, k);
+      z = k < hi - 2 ? A(k + 3, k) : 0.0;
     }
     {  // last step: a 2 x 2 reflector on rows/columns hi-1, hi
       const int k = hi - 1;
@@ -190,11 +192,24 @@ bool inverse_iteration(const std::vector<double>& F, int n, cd theta, std::vecto
 }  // namespace
 
 int harmonic_ritz(const double* Hbar, int m, int d, double* Y, double* theta_re, double* theta_im) {
+  // Work on Hbar / 2^e with 2^e near its largest entry (an exact scaling):
+  // F scales with Hbar, its eigenvectors do not, and products of entries
+  // (h^2, the QR shifts, the 3-vectors of the bulge chase) then neither
+  // underflow nor overflow for Hbar of any magnitude.
+  double amax = 0.0;
+  for (int i = 0; i < (m + 1) * m; ++i) {
+    if (!std::isfinite(Hbar[i])) return SLD_ERR_BREAKDOWN;
+    amax = std::max(amax, std::fabs(Hbar[i]));
+  }
+  if (amax == 0.0) return SLD_ERR_BREAKDOWN;
+  int ex = 0;
+  std::frexp(amax, &ex);
+  const double unscale = std::ldexp(1.0, ex);
   // F = H_m + h_{m+1,m}^2 f e_m^T with H_m^T f = e_m
   std::vector<double> F((size_t)m * m);
   for (int i = 0; i < m; ++i)
-    for (int j = 0; j < m; ++j) F[(size_t)i * m + j] = Hbar[(size_t)i * m + j];
-  const double h = Hbar[(size_t)m * m + (m - 1)];
+    for (int j = 0; j < m; ++j) F[(size_t)i * m + j] = std::ldexp(Hbar[(size_t)i * m + j], -ex);
+  const double h = std::ldexp(Hbar[(size_t)m * m + (m - 1)], -ex);
   if (h != 0.0) {
     std::vector<double> HT((size_t)m * m);
     for (int i = 0; i < m; ++i)
@@ -257,13 +272,13 @@ int harmonic_ritz(const double* Hbar, int m, int d, double* Y, double* theta_re,
     const cd ph = std::abs(y[big]) > 0.0 ? std::conj(y[big]) / std::abs(y[big]) : cd(1.0);
     for (cd& v : y) v *= ph;
     for (int i = 0; i < m; ++i) Y[(size_t)i * d + got] = y[i].real();
-    theta_re[got] = ev[k].real();
-    theta_im[got] = ev[k].imag();
+    theta_re[got] = ev[k].real() * unscale;
+    theta_im[got] = ev[k].imag() * unscale;
     ++got;
     if (cplx && got < d) {
       for (int i = 0; i < m; ++i) Y[(size_t)i * d + got] = y[i].imag();
-      theta_re[got] = ev[k].real();
-      theta_im[got] = -ev[k].imag();
+      theta_re[got] = ev[k].real() * unscale;
+      theta_im[got] = -ev[k].imag() * unscale;
       ++got;
     }
   }

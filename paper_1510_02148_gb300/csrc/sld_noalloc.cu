@@ -61,13 +61,18 @@ __global__ void k_restrict_finish(int d, int rows, const double* __restrict__ sc
   out[k] = t;
 }
 
-bool on_device(const void* p) {
+// True when the kernels of device `dev` may read p directly: device memory of
+// that same GPU, or managed memory.  Device memory of another GPU is refused:
+// this entry point copies nothing, and a direct read of a peer's memory
+// without peer access enabled is an illegal address.
+bool on_device(const void* p, int dev) {
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  if (at.type == cudaMemoryTypeManaged) return true;
+  return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
 }  // namespace
@@ -88,8 +93,9 @@ sld_status sld_restrict_noalloc(sld_system s, const double* v, double* out) {
   if (e != cudaSuccess) return na_fail(SLD_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
   if (dev != s->device || dev < 0 || dev >= kNoAllocMaxDevices)
     return na_fail(SLD_ERR_INVALID_ARG, "make the handle's device current before the call");
-  if (!on_device(v) || !on_device(out))
-    return na_fail(SLD_ERR_INVALID_ARG, "v and out must be device memory (this entry point stages nothing)");
+  if (!on_device(v, dev) || !on_device(out, dev))
+    return na_fail(SLD_ERR_INVALID_ARG,
+                   "v and out must be device memory of the handle's GPU (this entry point stages nothing)");
   double* scratch = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_mu);

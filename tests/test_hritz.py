@@ -119,3 +119,35 @@ def test_singular_and_non_finite_hessenberg(lib):
         lib.harmonic_ritz(np.triu(np.ones((66, 65)), -1), 2)
     with pytest.raises(lib.SldError, match="INVALID_ARG"):
         lib.harmonic_ritz(np.triu(np.ones((5, 4)), -1), 5)
+
+
+@pytest.mark.parametrize("scale", [2.0 ** -560, 1e-170, 1e150])
+def test_tiny_and_huge_hessenberg(lib, scale):
+    """Entries near 1e-170: unscaled, the products that form h^2 and the
+    bulge-chase 3-vectors underflow to exact zeros (the reflector step then
+    has nothing to act on); near 1e150 they overflow.  The eigenvalues scale
+    with H and the eigenvectors do not, so the result is the unit-scale one
+    times `scale`."""
+    rng = np.random.default_rng(21)
+    m = 12
+    H = np.triu(rng.standard_normal((m + 1, m)), -1) + 2.0 * np.eye(m + 1, m)
+    Y1, th1 = lib.harmonic_ritz(H, 4)
+    Ys, ths = lib.harmonic_ritz(H * scale, 4)
+    np.testing.assert_allclose(ths.real, th1.real * scale, rtol=1e-10, atol=1e-12 * scale)
+    np.testing.assert_allclose(ths.imag, th1.imag * scale, rtol=1e-10, atol=1e-12 * scale)
+    Q1, _ = np.linalg.qr(Y1)
+    Qs, _ = np.linalg.qr(Ys)
+    assert np.all(np.linalg.svd(Q1.T @ Qs, compute_uv=False) > 1 - 1e-9)
+
+
+def test_bulge_with_zero_column_keeps_chasing(lib):
+    """A block whose leading part is already upper triangular to rounding in
+    the first column (h_21 = 0 exactly, h_31 = 0): the active block splits
+    there, and the Francis steps of the lower block still converge."""
+    m = 8
+    rng = np.random.default_rng(3)
+    H = np.triu(rng.standard_normal((m + 1, m)), -1) + 3.0 * np.eye(m + 1, m)
+    H[1, 0] = 0.0
+    ev = np.linalg.eigvals(_F(H))
+    Y, theta = lib.harmonic_ritz(H, m)
+    np.testing.assert_allclose(np.sort_complex(theta), np.sort_complex(ev), rtol=1e-8, atol=1e-12)
