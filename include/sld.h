@@ -96,6 +96,16 @@ typedef struct {
   int debug_skip_barrier; /* test hook: CTA 0 skips the k-th barrier arrival of the
                              solve so that the other CTAs' bounded waits run out
                              (SLD_ERR_TIMEOUT); -1 = off (default) */
+  double fwd_tol;         /* mixed modes: a forward-error test on top of the residual
+                             test.  The refinement stops only after a step whose
+                             inner solve had a relative target (a cut of at least
+                             10x, not the 0.3 tol floor), reached it, and changed
+                             x by at most fwd_tol * ||x||: that change estimates
+                             the error of the previous iterate, which the step
+                             does not increase.  0 = 100 * tol (the default);
+                             < 0 = off (the residual test alone, fewer steps on
+                             high-contrast fields, larger error in the directions
+                             of the smallest eigenvalues). */
 } sld_options;
 
 typedef struct {
@@ -106,6 +116,9 @@ typedef struct {
   double solve_ms;         /* device time of the persistent solve kernel (CUDA events) */
   int kernel_path;         /* 1: TMA-pipelined sweeps (nx % 8 == 0), 0: register/shuffle sweeps,
                               2: batched launch (register/shuffle sweeps) */
+  double fwd_err_estimate; /* mixed modes: |d| / |x| of the last step that passed the
+                              forward-error test's conditions (see fwd_tol); -1 = none
+                              (SLD_FP64, or the test off and never met) */
 } sld_result;
 
 /* Fill *o with the defaults listed above. */
@@ -198,6 +211,9 @@ sld_status sld_deflation_info(sld_system s, int* d, int* k_requested, int* k_use
  *   b: n values, or NULL for the assembled right-hand side.
  *   o: options or NULL for the defaults.
  *   x: n values (output).  res: may be NULL.
+ * With the environment variable SLD_TRACE_REFINEMENT set, a mixed-mode
+ * solve prints |d_k| / |x_k| and ||r_k|| / ||b|| of its first 16
+ * refinement steps to stderr.
  * Errors: SLD_ERR_STATE (no deflation built), SLD_ERR_NOT_CONVERGED (x and
  * res still written), SLD_ERR_BREAKDOWN, SLD_ERR_TIMEOUT, SLD_ERR_CUDA.
  */

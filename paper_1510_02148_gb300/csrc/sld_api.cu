@@ -159,6 +159,7 @@ void sld_default_options(sld_options* o) {
   o->ctas_per_sm = 0;
   o->timeout_s = 2.0;
   o->debug_skip_barrier = -1;
+  o->fwd_tol = 0.0;
 }
 
 const char* sld_last_error(void) { return g_last_error.c_str(); }
@@ -441,6 +442,7 @@ sld_status sld_solve(sld_system s, const double* b, const sld_options* opt, doub
     return fail(SLD_ERR_INVALID_ARG, "precision must be SLD_FP64, SLD_FP32_IR or SLD_BF16COEF_IR");
   if (!(o.tol > 0) || !(o.tol < 1)) return fail(SLD_ERR_INVALID_ARG, "tol must be in (0, 1)");
   if (!(o.inner_tol > 0) || !(o.inner_tol < 1)) return fail(SLD_ERR_INVALID_ARG, "inner_tol must be in (0, 1)");
+  if (!std::isfinite(o.fwd_tol)) return fail(SLD_ERR_INVALID_ARG, "fwd_tol must be finite");
   if (o.maxiter < 1 || o.max_outer < 1) return fail(SLD_ERR_INVALID_ARG, "maxiter and max_outer must be >= 1");
   sld_status st = ensure_workspace(s, o.precision == SLD_FP32_IR, o.precision == SLD_BF16COEF_IR);
   if (st != SLD_OK) return st;
@@ -658,6 +660,7 @@ sld_status collect(sld_system s, const double* b_dev, double ms, double* x, sld_
   r->iterations = (int)out[sld::kOutIters];
   r->outer_steps = (int)out[sld::kOutOuter];
   r->recursive_relres = out[sld::kOutBB] > 0 ? std::sqrt(out[sld::kOutRecRR] / out[sld::kOutBB]) : 0.0;
+  r->fwd_err_estimate = out[sld::kOutFwd];
   r->solve_ms = ms;
   r->kernel_path = 2;
   if (dev_status != 0) return fail((sld_status)dev_status, "a device-side wait timed out (team barrier)");
@@ -701,7 +704,8 @@ sld_status sld_batch_create(sld_system* systems, int count, const sld_options* o
   if (opt) o = *opt;
   if (o.precision != SLD_FP64 && o.precision != SLD_FP32_IR)
     return fail(SLD_ERR_INVALID_ARG, "batched solves take SLD_FP64 or SLD_FP32_IR");
-  if (!(o.tol > 0) || !(o.tol < 1) || !(o.inner_tol > 0) || !(o.inner_tol < 1) || o.maxiter < 1 || o.max_outer < 1)
+  if (!(o.tol > 0) || !(o.tol < 1) || !(o.inner_tol > 0) || !(o.inner_tol < 1) || !std::isfinite(o.fwd_tol) ||
+      o.maxiter < 1 || o.max_outer < 1)
     return fail(SLD_ERR_INVALID_ARG, "bad tolerances or iteration caps");
   for (int k = 0; k < count; ++k) {
     sld_system s = systems[k];

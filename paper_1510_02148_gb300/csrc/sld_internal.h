@@ -75,13 +75,17 @@ struct SolveArgs {
   double* out;            // results: see kOut*
   SyncArgs sy;
   double tol, inner_tol;
+  double fwd_tol;         // mixed forms: forward-error bound of the refinement (< 0: off)
   int maxiter, max_outer;
   int fp64;               // 1: inner in FP64, single inner solve + finalisation
   int bf16;               // 1: inner faces stored as BF16
 };
 
 enum {
-  kOutIters = 0, kOutOuter, kOutRR, kOutBB, kOutStatus, kOutRecRR, kOutCount = 8
+  kOutIters = 0, kOutOuter, kOutRR, kOutBB, kOutStatus, kOutRecRR, kOutFwd,
+  // refinement trace (mixed forms): for outer step k < kTraceSteps, the
+  // squared norm of its correction at kOutTrace + 2k, its residual at +2k+1
+  kOutTrace = 8, kTraceSteps = 16, kOutCount = kOutTrace + 2 * kTraceSteps
 };
 
 }  // namespace sld

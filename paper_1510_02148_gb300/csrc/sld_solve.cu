@@ -26,6 +26,7 @@
 // With x = 0 this is x = Z E^{-1} Z^T b and rhat_0 = P b; after an inner solve
 // it is x = x + xhat + Z E^{-1} Z^T (b - A (x + xhat)), i.e. x* + P^T xhat.
 #include <cstdlib>
+#include <cstdio>
 #include <cstring>
 #include <vector>
 
@@ -764,6 +765,7 @@ void fill_args(sld_system s, const double* b_dev, const sld_options& o, SolveArg
   a.sy.skip_epoch = o.debug_skip_barrier >= 0 ? o.debug_skip_barrier + 1 : 0;
   a.tol = o.tol;
   a.inner_tol = o.inner_tol;
+  a.fwd_tol = o.fwd_tol == 0.0 ? 100.0 * o.tol : o.fwd_tol;
   a.maxiter = o.maxiter;
   a.max_outer = fp64 ? 1 : o.max_outer;
   a.fp64 = fp64 ? 1 : 0;
@@ -816,6 +818,15 @@ int run_solve(sld_system s, const double* b_dev, const sld_options& o, sld_resul
   res->iterations = (int)out[kOutIters];
   res->outer_steps = (int)out[kOutOuter];
   res->recursive_relres = out[kOutBB] > 0 ? std::sqrt(out[kOutRecRR] / out[kOutBB]) : 0.0;
+  res->fwd_err_estimate = out[kOutFwd];
+  if (!fp64 && std::getenv("SLD_TRACE_REFINEMENT")) {
+    // |d_k| / |x_k| and ||r_k|| / ||b|| per refinement step, to stderr
+    std::fprintf(stderr, "sld refinement: %d steps, %d iterations, estimate %.3e\n", res->outer_steps,
+                 res->iterations, res->fwd_err_estimate);
+    for (int k = 0; k < res->outer_steps && k < kTraceSteps; ++k)
+      std::fprintf(stderr, "  step %2d  |d|/|x| %.3e  |r|/|b| %.3e\n", k + 1, std::sqrt(out[kOutTrace + 2 * k]),
+                   std::sqrt(out[kOutTrace + 2 * k + 1]));
+  }
   res->solve_ms = ms;
   if (dev_status != 0) {
     *msg = dev_status == SLD_ERR_TIMEOUT ? "a device-side wait timed out (grid barrier)" : "device error";

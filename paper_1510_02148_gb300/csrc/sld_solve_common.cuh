@@ -310,14 +310,15 @@ __device__ void sweep_O1(const SolveArgs& a, double* sacc, double* red, double* 
   if (threadIdx.x == 0) part_row[(int64_t)(a.dk + 3) * a.pstride] = bsum;
 }
 
-// O2: x += xhat + Z y, rhat = r' - A Z y, z = M^{-1} rhat, xhat = p = 0
+// O2: x += xhat + Z y, rhat = r' - A Z y, z = M^{-1} rhat, xhat = p = 0;
+// also ||x_new - x||^2 and ||x_new||^2 for the refinement's forward-error test
 template <typename T>
 __device__ void sweep_O2(const SolveArgs& a, const double* Yd, double* red, double* part_row) {
   T* xh = static_cast<T*>(a.xh);
   T* zb = static_cast<T*>(a.z);
   T* p0 = static_cast<T*>(a.p0);
   T* p1 = static_cast<T*>(a.p1);
-  double rr = 0.0, rho = 0.0;
+  double rr = 0.0, rho = 0.0, dd = 0.0, xx = 0.0;
   const int64_t stride = (int64_t)a.sy.ncta * blockDim.x;
   CellWalk c;
   for (c.init(a, (int64_t)team_rank(a.sy) * blockDim.x + threadIdx.x, stride); c.ok(); c.next()) {
@@ -330,7 +331,11 @@ __device__ void sweep_O2(const SolveArgs& a, const double* Yd, double* red, doub
       Zy += (double)a.ZL32[i * kMaxL + j] * yj;
     }
     const double rh = a.r64[i] - AZy;
-    a.x[i] = a.x[i] + (double)xh[ip] + Zy;
+    const double xo = a.x[i];
+    const double xn = xo + (double)xh[ip] + Zy;
+    a.x[i] = xn;
+    dd += (xn - xo) * (xn - xo);  // the change this step applies to x
+    xx += xn * xn;
     const T zt = (T)(rh * (a.invdi ? (double)a.invdi[ip] : a.invdiag64[i]));
     zb[ip] = zt;
     xh[ip] = T(0);
@@ -342,9 +347,13 @@ __device__ void sweep_O2(const SolveArgs& a, const double* Yd, double* red, doub
   fence_proxy_async();  // z, xhat, p stores before the next sweep's TMA reads
   const double s1 = block_sum(rho, red);
   const double s2 = block_sum(rr, red);
+  const double s4 = block_sum(dd, red);
+  const double s5 = block_sum(xx, red);
   if (threadIdx.x == 0) {
     part_row[(int64_t)(a.dk + 1) * a.pstride] = s1;
     part_row[(int64_t)(a.dk + 2) * a.pstride] = s2;
+    part_row[(int64_t)(a.dk + 4) * a.pstride] = s4;
+    part_row[(int64_t)(a.dk + 5) * a.pstride] = s5;
   }
 }
 
@@ -429,6 +438,9 @@ __device__ double cta_take_y(const SolveArgs& a, T* Y, double* red) {
 // All decisions use scalars every CTA reduces in the same order, so every
 // CTA takes the same branches.
 // ---------------------------------------------------------------------------
+// Squared least residual cut of an inner solve in the mixed forms (10x).
+constexpr double kMinCut2 = 0.01;
+
 template <typename T, bool WACC, class SweepA, class SweepB>
 __device__ void solve_body(const SolveArgs& a, double* acc, double* Yd, T* Y, double* red, SweepA&& sweepA,
                            SweepB&& sweepB) {
@@ -436,6 +448,18 @@ __device__ void solve_body(const SolveArgs& a, double* acc, double* Yd, T* Y, do
   unsigned epoch = 0;
   const double tol2 = a.tol * a.tol;
   double bb = 0.0, rr_outer = 0.0, rho = 0.0, rec_rr = 0.0;
+  // Refinement state of the forward-error test (mixed forms), in shared
+  // memory so that it holds no registers during the sweeps: the inner
+  // target of the last step, whether it was relative (not the 0.3 tol
+  // floor), the last verified |d| / |x| (reported at exit).  Every thread
+  // reads it after a CTA barrier; thread 0 writes it after another one.
+  enum { kTgtPrev = 0, kRelPrev, kFwdRel, kFsCount };
+  __shared__ double fs[kFsCount];
+  if (threadIdx.x == 0) {
+    fs[kTgtPrev] = 0.0;
+    fs[kRelPrev] = 0.0;
+    fs[kFwdRel] = -1.0;
+  }
   int its = 0, outer = 0, status = 0;
   bool converged = false;
   bool failed = false;
@@ -460,10 +484,42 @@ __device__ void solve_body(const SolveArgs& a, double* acc, double* Yd, T* Y, do
       if (outer >= 2) break;  // x = x* + P^T xhat written: done
     } else {
       rec_rr = rr_outer;
-      if (rr_outer <= tol2 * bb) { converged = true; break; }
-      if (outer > a.max_outer || its >= a.maxiter) break;
+      double dd, xx;
+      cta_scalar2(a, 4, 5, red, &dd, &xx);
+      if (team_rank(a.sy) == 0 && threadIdx.x == 0 && outer <= kTraceSteps) {
+        a.out[kOutTrace + 2 * (outer - 1)] = dd / fmax(xx, 1e-300);
+        a.out[kOutTrace + 2 * (outer - 1) + 1] = rr_outer / fmax(bb, 1e-300);
+      }
+      const bool res_ok = rr_outer <= tol2 * bb;
+      // The residual test alone lets errors along the smallest eigenvalues
+      // of the deflated operator through (their residual is tiny), and
+      // restarted low-precision inner solves resolve those modes less well
+      // than one long FP64 CG run.  So the refinement also checks its
+      // forward error: a step whose inner solve had a relative target (a
+      // residual cut, not the 0.3 tol floor) and reached it applies a
+      // correction d_k ~ the previous error e_{k-1}, and e_k <= e_{k-1}
+      // (the refinement contracts the energy norm).  Accept once such a
+      // step has |d_k| <= fwd_tol |x|.  Step 1 is the FP64 coarse solution
+      // x* (exact to rounding): no low-precision step has touched x yet.
+      const bool verified = outer >= 3 && fs[kRelPrev] != 0.0 && rr_outer <= 4.0 * fs[kTgtPrev];
+      const double drel = xx > 0.0 ? sqrt(dd / xx) : 0.0;
+      const bool fwd_ok = a.fwd_tol < 0.0 || outer == 1 || (verified && drel <= a.fwd_tol);
+      // next inner target: inner_tol relative, floored at 0.3 tol ||b||, and
+      // at least a 10x cut of the residual (so that the steps after the
+      // residual test has passed are relative ones)
+      const double floor2 = 0.09 * tol2 * bb;
+      const double tgt2n = fmin(fmax(a.inner_tol * a.inner_tol * rr_outer, floor2), kMinCut2 * rr_outer);
+      __syncthreads();  // every thread has read fs
+      if (threadIdx.x == 0) {
+        if (verified) fs[kFwdRel] = drel;
+        fs[kTgtPrev] = tgt2n;
+        fs[kRelPrev] = (tgt2n < floor2 || a.inner_tol * a.inner_tol * rr_outer > floor2) ? 1.0 : 0.0;
+      }
+      if (res_ok && fwd_ok) { converged = true; break; }
+      if (outer > a.max_outer || its >= a.maxiter) { converged = res_ok; break; }
     }
-    const double tgt2 = a.fp64 ? tol2 * bb : fmax(a.inner_tol * a.inner_tol * rr_outer, 0.09 * tol2 * bb);
+    const double tgt2 = a.fp64 ? tol2 * bb
+                               : fmin(fmax(a.inner_tol * a.inner_tol * rr_outer, 0.09 * tol2 * bb), kMinCut2 * rr_outer);
     // ---- inner deflated CG ----
     double beta = 0.0;
     int pold = 0;
@@ -505,6 +561,7 @@ __device__ void solve_body(const SolveArgs& a, double* acc, double* Yd, T* Y, do
     a.out[kOutBB] = bb;
     a.out[kOutStatus] = failed ? -1.0 : (status ? (double)status : (converged ? 0.0 : (double)SLD_ERR_NOT_CONVERGED));
     a.out[kOutRecRR] = rec_rr;
+    a.out[kOutFwd] = fs[kFwdRel];
   }
 }
 

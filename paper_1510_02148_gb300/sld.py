@@ -54,12 +54,13 @@ class Bc(C.Structure):
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("tol", C.c_double), ("inner_tol", C.c_double),
                 ("maxiter", C.c_int), ("max_outer", C.c_int), ("ctas_per_sm", C.c_int),
-                ("timeout_s", C.c_double), ("debug_skip_barrier", C.c_int)]
+                ("timeout_s", C.c_double), ("debug_skip_barrier", C.c_int), ("fwd_tol", C.c_double)]
 
 
 class Result(C.Structure):
     _fields_ = [("iterations", C.c_int), ("outer_steps", C.c_int), ("true_relres", C.c_double),
-                ("recursive_relres", C.c_double), ("solve_ms", C.c_double), ("kernel_path", C.c_int)]
+                ("recursive_relres", C.c_double), ("solve_ms", C.c_double), ("kernel_path", C.c_int),
+                ("fwd_err_estimate", C.c_double)]
 
 
 class GmresInfo(C.Structure):
@@ -170,6 +171,7 @@ class SolveInfo:
     solve_ms: float
     status: int
     kernel_path: int = 0
+    fwd_err_estimate: float = -1.0
 
 
 class System:
@@ -266,7 +268,7 @@ class System:
         r = Result()
         st = load().sld_solve(self._h, _ptr(b, np.float64), C.byref(o), _ptr(x, np.float64), C.byref(r))
         info = SolveInfo(r.iterations, r.outer_steps, r.true_relres, r.recursive_relres, r.solve_ms, st,
-                         r.kernel_path)
+                         r.kernel_path, r.fwd_err_estimate)
         if st != OK and raise_on_error:
             _check(st)
         return x, info
@@ -378,7 +380,7 @@ class Batch:
         res = (Result * n)()
         st = load().sld_batch_solve(self._h, bptr, xptr, res)
         infos = [SolveInfo(r.iterations, r.outer_steps, r.true_relres, r.recursive_relres, r.solve_ms, st,
-                           r.kernel_path) for r in res]
+                           r.kernel_path, r.fwd_err_estimate) for r in res]
         if st != OK and raise_on_error:
             _check(st)
         return xs, infos

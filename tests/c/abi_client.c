@@ -24,6 +24,7 @@ int main(void) {
   CHECK(o.tol == 1e-9);
   CHECK(o.maxiter == 20000 && o.max_outer == 40 && o.ctas_per_sm == 0);
   CHECK(o.debug_skip_barrier == -1);
+  CHECK(o.fwd_tol == 0.0);
   /* argument checks happen before any device work */
   double x = 0.0;
   CHECK(sld_solve(NULL, NULL, &o, &x, NULL) == SLD_ERR_INVALID_ARG);

@@ -54,6 +54,9 @@ def test_batched_matches_oracle(sld, oracle_mod, precision):
             tight = oracle_mod.dpcg(A, lab, P.d, tol=1e-13)
             assert true <= 1e-9
             assert _energy_relerr(A, x, tight.x) <= max(1e-9, 5 * _energy_relerr(A, ref.x, tight.x)), P.name
+            e_gpu = np.linalg.norm(x - tight.x) / np.linalg.norm(tight.x)
+            e_ref = np.linalg.norm(ref.x - tight.x) / np.linalg.norm(tight.x)
+            assert e_gpu <= max(1e-7, 3 * e_ref), (P.name, e_gpu, e_ref)
     bt.close()
     for s in systems:
         s.close()
