@@ -18,7 +18,8 @@ constexpr int kTY = 8;                  // rows per tile
 constexpr int kWarps = kTY + 2;         // + two halo-row warps
 constexpr int kThreads = kWarps * 32;   // 320
 constexpr int kMaxD = 4096;             // largest d (labels) the kernels take
-constexpr int kWarpAccMaxD = 256;       // per-warp label accumulators up to this d
+constexpr int kWarpAccMaxD = 256;       // per-warp label rows in shared memory up to this d (global above)
+constexpr int kGaccRows = kWarps > 8 ? kWarps : 8;  // warp rows per CTA in the global label-sum rows
 constexpr int kPartScalars = 8;         // scalar slots after the dk coarse sums
 constexpr int kMaxL = 8;                // extra dense deflation vectors (slots per cell)
 
@@ -67,6 +68,10 @@ struct SolveArgs {
   // inner operator and state, element type per mode (double or float)
   const void *Txi, *Tyi, *Tzi;
   void *z, *p0, *p1, *xh;
+  // per-warp label-sum rows in global memory (d > kWarpAccMaxD): CTA c owns
+  // gacc[c * gacc_stride .. + rows * d), indexed by blockIdx.x
+  double* gacc;
+  int64_t gacc_stride;
   // reductions
   double* part;           // [grid][pstride]
   int pstride;
@@ -129,6 +134,8 @@ struct sld_system_s {
   unsigned* bar = nullptr;
   int* status = nullptr;
   int part_rows = 0;
+  double* gacc = nullptr;  // global per-warp label-sum rows (d > kWarpAccMaxD), grown on demand
+  size_t gacc_cap = 0;     // doubles
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
 
@@ -155,6 +162,8 @@ cudaError_t launch_apply_A(sld_system s, const double* x, double* y);
 cudaError_t launch_restrict(sld_system s, const double* v, double* out);
 cudaError_t launch_residual(sld_system s, const double* b, const double* x, double* partial_out,
                             double* rr_host, double* bb_host);
+// s->gacc with room for `doubles` values (kept, grown on demand)
+cudaError_t ensure_gacc(sld_system s, size_t doubles);
 // sld_solve_tma.cu
 bool tma_eligible(const Geo& g, bool fp64);
 int launch_solve_tma(sld_system s, SolveArgs& a, const sld_options& o, float* ms, std::string* msg);
@@ -201,6 +210,7 @@ struct BatchPlan {
   size_t smem = 0;
   SolveArgs* d_args = nullptr;
   int* d_cta = nullptr;
+  double* d_gacc = nullptr;  // global per-warp label-sum rows (dmax > kWarpAccMaxD)
   cudaStream_t stream = nullptr;  // the batch's own stream (capture and launch), not owned here
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;

@@ -47,7 +47,7 @@ struct Sm {
   T* P;        // [2][kTY+2][RS]   published neighbour values
   T* Ty;       // [2][kTY+1][TX]   Ty of rows y0-1 .. y0+kTY-1
   T* Txh;      // [2][kTY]         Tx of the face left of the tile
-  double* acc; // [kWarps][d] or [d]  label sums
+  double* acc; // [kWarps][d] label sums: shared memory, or the CTA's global rows (d > kWarpAccMaxD)
   double* Yd;  // [d] coarse correction, FP64
   T* Y;        // [d] coarse correction, inner precision
   double* red; // [64] block reduction scratch
@@ -61,7 +61,7 @@ __host__ __device__ constexpr size_t smem_bytes(int d, int dk) {
   b += sizeof(T) * 2 * (kTY + 1) * C::TX;
   b += sizeof(T) * 2 * kTY;
   b = (b + 15) / 16 * 16;
-  b += sizeof(double) * (size_t)(WACC ? kWarps : 1) * d;
+  b += sizeof(double) * (size_t)(WACC ? kWarps : 0) * d;
   b += sizeof(double) * dk;
   b += sizeof(T) * dk;
   b = (b + 15) / 16 * 16;
@@ -82,7 +82,7 @@ __device__ Sm<T> carve(unsigned char* base, int d, int dk) {
   o += sizeof(T) * 2 * kTY;
   o = (o + 15) / 16 * 16;
   s.acc = reinterpret_cast<double*>(base + o);
-  o += sizeof(double) * (size_t)(WACC ? kWarps : 1) * d;
+  o += sizeof(double) * (size_t)(WACC ? kWarps : 0) * d;
   s.Yd = reinterpret_cast<double*>(base + o);
   o += sizeof(double) * dk;
   s.Y = reinterpret_cast<T*>(base + o);
@@ -176,9 +176,9 @@ __device__ void sweep_A(const SolveArgs& a, const Sm<T>& sm, const T* zb, const 
   const Geo& g = a.g;
   const int d = a.d;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int k = threadIdx.x; k < (WACC ? kTY : 1) * d; k += blockDim.x) sm.acc[k] = 0.0;
+  for (int k = threadIdx.x; k < kTY * d; k += blockDim.x) sm.acc[k] = 0.0;
   __syncthreads();
-  LabelAcc<T, WACC> la;
+  LabelAcc<T, true> la;
   la.init(a.lab_L);
   double dgam = 0.0;
   const int tr = team_rank(a.sy);
@@ -370,11 +370,7 @@ __device__ void sweep_A(const SolveArgs& a, const Sm<T>& sm, const T* zb, const 
   const double gsum = block_sum(dgam, sm.red);  // contains __syncthreads
   for (int k = threadIdx.x; k < d; k += blockDim.x) {
     double t = 0.0;
-    if constexpr (WACC) {
-      for (int w = 0; w < kTY; ++w) t += sm.acc[w * d + k];
-    } else {
-      t = sm.acc[k];
-    }
+    for (int w = 0; w < kTY; ++w) t += sm.acc[w * d + k];  // warp order: deterministic
     part_row[(int64_t)(k) * a.pstride] = t;
   }
   if (threadIdx.x == 0) part_row[(int64_t)(a.dk + 0) * a.pstride] = gsum;
@@ -618,7 +614,8 @@ __device__ void sweep_B(const SolveArgs& a, const Sm<T>& sm, const T* p, T* zb, 
 
 template <typename T, int CX, bool WACC>
 __device__ __forceinline__ void solve_generic(const SolveArgs& a, unsigned char* smem_raw) {
-  const Sm<T> sm = carve<T, CX, WACC>(smem_raw, a.d, a.dk);
+  Sm<T> sm = carve<T, CX, WACC>(smem_raw, a.d, a.dk);
+  if (!WACC) sm.acc = a.gacc + (int64_t)blockIdx.x * a.gacc_stride;
   const T* Fx = static_cast<const T*>(a.Txi);
   const T* Fy = static_cast<const T*>(a.Tyi);
   const T* Fz = static_cast<const T*>(a.Tzi);
@@ -678,6 +675,15 @@ int launch(sld_system s, SolveArgs& a, const sld_options& o, float* ms, std::str
   if (G > s->part_rows) G = s->part_rows;
   a.sy.cta0 = 0;
   a.sy.ncta = G;
+  if (!WACC) {
+    a.gacc_stride = (int64_t)kGaccRows * a.d;
+    e = ensure_gacc(s, (size_t)G * a.gacc_stride);
+    if (e != cudaSuccess) {
+      *msg = std::string("label-sum rows: ") + cudaGetErrorString(e);
+      return e == cudaErrorMemoryAllocation ? SLD_ERR_OOM : SLD_ERR_CUDA;
+    }
+    a.gacc = s->gacc;
+  }
   void* args[] = {&a};
   cudaEventRecord(s->ev0, s->stream);
   e = cudaLaunchCooperativeKernel((void*)kern, dim3(G), dim3(kThreads), args, smem, s->stream);
@@ -756,6 +762,8 @@ void fill_args(sld_system s, const double* b_dev, const sld_options& o, SolveArg
   a.xh = s->xh;
   a.part = s->part;
   a.pstride = s->part_rows;  // column-major partials: one slot per CTA
+  a.gacc = nullptr;          // set at launch when d > kWarpAccMaxD
+  a.gacc_stride = 0;
   a.s_glob = s->s_glob;
   a.y_glob = s->y_glob;
   a.out = s->out;
@@ -921,7 +929,9 @@ void batch_free(BatchPlan* p) {
   if (p->d_args) cudaFree(p->d_args);
   if (p->d_cta) cudaFree(p->d_cta);
   if (p->d_maps) cudaFree(p->d_maps);
+  if (p->d_gacc) cudaFree(p->d_gacc);
   p->d_maps = nullptr;
+  p->d_gacc = nullptr;
   p->exec = nullptr;
   p->graph = nullptr;
   p->d_args = nullptr;
@@ -1024,7 +1034,16 @@ int batch_build(sld_system* sys, int count, const sld_options& o, int per_sm, do
     args[k].sy.ncta = p->teams[k];
     for (int c = 0; c < p->teams[k]; ++c) cta_sys.push_back(k);
   }
-  cudaError_t e = cudaMalloc(&p->d_args, sizeof(SolveArgs) * count);
+  cudaError_t e = cudaSuccess;
+  if (!p->wacc) {  // the CTAs' global label-sum rows, one slice per CTA of the launch
+    const int64_t stride = (int64_t)kGaccRows * dmax;
+    e = cudaMalloc(&p->d_gacc, sizeof(double) * (size_t)used * stride);
+    for (int k = 0; k < count; ++k) {
+      args[k].gacc = p->d_gacc;
+      args[k].gacc_stride = stride;
+    }
+  }
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_args, sizeof(SolveArgs) * count);
   if (e == cudaSuccess) e = cudaMalloc(&p->d_cta, sizeof(int) * used);
   if (e == cudaSuccess && p->tma) {
     std::vector<unsigned char> maps(tma_maps_bytes() * count);

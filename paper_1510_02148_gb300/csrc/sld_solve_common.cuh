@@ -247,8 +247,9 @@ __device__ __forceinline__ int acc_rows() { return (int)(blockDim.x >> 5); }
 
 // O1: r' = b - A (x + xhat), s = Z^T r', ||b||^2
 // The label sums use the run-sum accumulator below (FP64): groups summed in a
-// fixed order and, for d <= kWarpAccMaxD, added into the warp's own row of
-// shared accumulators, so the result does not depend on warp scheduling.
+// fixed order and added into the warp's own row of accumulators (shared
+// memory for d <= kWarpAccMaxD, the CTA's global rows above), so the result
+// does not depend on warp scheduling.
 
 template <typename T, bool WACC>
 __device__ void sweep_O1(const SolveArgs& a, double* sacc, double* red, double* part_row) {
@@ -256,7 +257,7 @@ __device__ void sweep_O1(const SolveArgs& a, double* sacc, double* red, double* 
   const int d = a.d;
   const int warp = threadIdx.x >> 5;
   const T* xh = static_cast<const T*>(a.xh);
-  for (int k = threadIdx.x; k < (WACC ? acc_rows() : 1) * d; k += blockDim.x) sacc[k] = 0.0;
+  for (int k = threadIdx.x; k < acc_rows() * d; k += blockDim.x) sacc[k] = 0.0;
   __syncthreads();
   double bb = 0.0;
   double sl[kMaxL] = {};  // Z_L^T r' (extra columns)
@@ -268,7 +269,7 @@ __device__ void sweep_O1(const SolveArgs& a, double* sacc, double* red, double* 
   const int64_t nround = chunk / blockDim.x;
   CellWalk c;
   c.init(a, (int64_t)team_rank(a.sy) * chunk + threadIdx.x, blockDim.x);
-  LabelAcc<double, WACC> la;
+  LabelAcc<double, true> la;
   la.init(a.lab_L);
   for (int64_t rnd = 0; rnd < nround; ++rnd, c.next()) {
     const int64_t i = c.i;
@@ -300,11 +301,7 @@ __device__ void sweep_O1(const SolveArgs& a, double* sacc, double* red, double* 
   const double bsum = block_sum(bb, red);
   for (int k = threadIdx.x; k < d; k += blockDim.x) {
     double t = 0.0;
-    if constexpr (WACC) {
-      for (int w = 0; w < acc_rows(); ++w) t += sacc[w * d + k];
-    } else {
-      t = sacc[k];
-    }
+    for (int w = 0; w < acc_rows(); ++w) t += sacc[w * d + k];  // warp order: deterministic
     part_row[(int64_t)(k) * a.pstride] = t;
   }
   if (threadIdx.x == 0) part_row[(int64_t)(a.dk + 3) * a.pstride] = bsum;

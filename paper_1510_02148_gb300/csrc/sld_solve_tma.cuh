@@ -257,7 +257,7 @@ __device__ bool sweep_tma(const SolveArgs& a, const Maps& mp, const Ring<S>& rg,
   T* zbw = static_cast<T*>(a.z);
   T* xhw = static_cast<T*>(a.xh);
   if constexpr (IS_A) {
-    for (int k = tid; k < (WACC ? C::kAcc : 1) * d; k += blockDim.x) sacc[k] = 0.0;
+    for (int k = tid; k < C::kAcc * d; k += blockDim.x) sacc[k] = 0.0;
   }
   const int tr = team_rank(a.sy);
   const int64_t t0 = a.ntiles * tr / a.sy.ncta, t1 = a.ntiles * (tr + 1) / a.sy.ncta;
@@ -284,7 +284,7 @@ __device__ bool sweep_tma(const SolveArgs& a, const Maps& mp, const Ring<S>& rg,
   __syncthreads();
   refill();
   uint64_t item = gitem;
-  LabelAcc<T, WACC> la;
+  LabelAcc<T, true> la;  // per-warp rows (shared or global): deterministic
   la.init(a.lab_L);
   T acc1 = T(0), acc2 = T(0);
   double dacc1 = 0.0, dacc2 = 0.0;
@@ -608,11 +608,7 @@ __device__ bool sweep_tma(const SolveArgs& a, const Maps& mp, const Ring<S>& rg,
     const double gsum = block_sum(dacc1, red);
     for (int k = tid; k < d; k += blockDim.x) {
       double s = 0.0;
-      if constexpr (WACC) {
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sacc[w * d + k];
-      } else {
-        s = sacc[k];
-      }
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sacc[w * d + k];  // warp order: deterministic
       part_row[(int64_t)(k) * a.pstride] = s;
     }
     if (tid == 0) part_row[(int64_t)(a.dk + 0) * a.pstride] = gsum;
@@ -647,7 +643,7 @@ __host__ __device__ constexpr size_t tma_smem_bytes(int d, int dk) {
   size_t b = C::SLOT * S;
   b += 8 * S;
   b = (b + 15) / 16 * 16;
-  b += sizeof(double) * (size_t)(WACC ? C::kAcc : 1) * d;
+  b += sizeof(double) * (size_t)(WACC ? C::kAcc : 0) * d;
   b += sizeof(double) * dk;
   b += sizeof(T) * dk;
   b = (b + 15) / 16 * 16;
@@ -667,8 +663,8 @@ __device__ __forceinline__ void tma_body(const SolveArgs& a, const Maps& mp, int
   rg.full = reinterpret_cast<uint64_t*>(smem_raw + o);
   o += 8 * S;
   o = (o + 15) / 16 * 16;
-  double* acc = reinterpret_cast<double*>(smem_raw + o);
-  o += sizeof(double) * (size_t)(WACC ? C::kAcc : 1) * a.d;
+  double* acc = WACC ? reinterpret_cast<double*>(smem_raw + o) : a.gacc + (int64_t)blockIdx.x * a.gacc_stride;
+  o += sizeof(double) * (size_t)(WACC ? C::kAcc : 0) * a.d;
   double* Yd = reinterpret_cast<double*>(smem_raw + o);
   o += sizeof(double) * a.dk;
   T* Y = reinterpret_cast<T*>(smem_raw + o);
@@ -809,6 +805,15 @@ int launch_tma(sld_system s, SolveArgs& a, const sld_options& o, float* ms, std:
   if (G > s->part_rows) G = s->part_rows;
   a.sy.cta0 = 0;
   a.sy.ncta = G;
+  if (!WACC) {
+    a.gacc_stride = (int64_t)kGaccRows * a.d;
+    e = ensure_gacc(s, (size_t)G * a.gacc_stride);
+    if (e != cudaSuccess) {
+      *msg = std::string("label-sum rows: ") + cudaGetErrorString(e);
+      return e == cudaErrorMemoryAllocation ? SLD_ERR_OOM : SLD_ERR_CUDA;
+    }
+    a.gacc = s->gacc;
+  }
   void* args[] = {&a, &mp, &ntx};
   cudaEventRecord(s->ev0, s->stream);
   e = cudaLaunchCooperativeKernel((void*)kern, dim3(G), dim3(16 * TY), args, smem, s->stream);

@@ -108,3 +108,31 @@ def test_batched_rejects(sld):
         sld.Batch([s], precision=sld.BF16COEF_IR)
     assert e.value.status == sld.ERR_INVALID_ARG
     s.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "fp32ir"])
+def test_batched_large_d_repeatable(sld, oracle_mod, precision):
+    """A batch whose largest d (512) takes the global per-warp label rows:
+    each system matches the oracle and a second launch repeats bit for bit."""
+    probs = [W.lognormal_point_source(64, 64, 32, 4, (8, 8, 4), seed=21),
+             W.lognormal_point_source(48, 40, 24, 4, (2, 2, 2), seed=22)]
+    systems = [sld.from_problem(P) for P in probs]
+    bt = sld.Batch(systems, precision=precision)
+    xs1, infos1 = bt.solve()
+    xs1 = [x.copy() for x in xs1]
+    xs2, infos2 = bt.solve()
+    for P, x1, x2, i1, i2 in zip(probs, xs1, xs2, infos1, infos2):
+        assert i1.iterations == i2.iterations and np.array_equal(x1, x2), P.name
+        A = oracle_mod.assemble(P.K, P.q, P.bc_type, P.bc_value)
+        lab = oracle_mod.labels(P.K, P.S, P.tau, P.L)
+        ref = oracle_mod.dpcg(A, lab, P.d, tol=P.tol)
+        if precision == 0:
+            assert np.linalg.norm(x1 - ref.x) / np.linalg.norm(ref.x) <= 1e-7
+            assert abs(i1.iterations - ref.iterations) <= 2
+        else:
+            tight = oracle_mod.dpcg(A, lab, P.d, tol=1e-13)
+            e = np.linalg.norm(x1 - tight.x) / np.linalg.norm(tight.x)
+            assert e <= max(1e-7, 3 * np.linalg.norm(ref.x - tight.x) / np.linalg.norm(tight.x))
+    bt.close()
+    for s in systems:
+        s.close()

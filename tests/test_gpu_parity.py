@@ -192,10 +192,13 @@ def test_solve_given_rhs_and_device_buffers(sld, oracle_mod):
     s.close()
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_repeat_solves_identical(sld, precision):
-    """Solves are bitwise repeatable (fixed-order reductions, d <= 256)."""
-    P = W.lognormal_point_source(64, 64, 32, 4, (2, 2, 2), seed=3)
+@pytest.mark.parametrize("precision", [0, 1, 2])
+@pytest.mark.parametrize("S", [(2, 2, 2), (8, 8, 4)], ids=["d16", "d512"])
+def test_repeat_solves_identical(sld, precision, S):
+    """Solves are bitwise repeatable: every reduction has a fixed order (the
+    label sums go through per-warp rows, in shared memory for d <= 256 and
+    in global memory above, summed in warp order)."""
+    P = W.lognormal_point_source(64, 64, 32, 4, S, seed=3)
     s = sld.from_problem(P)
     x1, i1 = s.solve(precision=precision)
     x2, i2 = s.solve(precision=precision)
@@ -343,4 +346,26 @@ def test_forward_error_test_of_the_refinement(sld, oracle_mod):
     assert i2.fwd_err_estimate == -1.0
     with pytest.raises(sld.SldError):
         s.solve(precision=sld.FP32_IR, fwd_tol=float("nan"))
+    s.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_generic_path_large_d(sld, oracle_mod, precision, monkeypatch):
+    """The register-sweep kernel with d = 512 (label sums in global per-warp
+    rows): the FP64 solve matches the oracle (1e-7, +-2 iterations), the
+    FP32-inner one reaches its bar, and both repeat bit for bit."""
+    monkeypatch.setenv("SLD_SOLVER_PATH", "generic")
+    P = W.lognormal_point_source(72, 64, 32, 4, (8, 8, 4), seed=5)
+    A, lab = _oracle_setup(oracle_mod, P)
+    ref = oracle_mod.dpcg(A, lab, P.d, tol=P.tol)
+    s = sld.from_problem(P)
+    x1, i1 = s.solve(precision=precision)
+    x2, i2 = s.solve(precision=precision)
+    assert i1.kernel_path == 0 and P.d == 512
+    assert i1.iterations == i2.iterations and np.array_equal(x1, x2)
+    if precision == 0:
+        assert _relerr(x1, ref.x) <= 1e-7 and abs(i1.iterations - ref.iterations) <= 2
+    else:
+        tight = oracle_mod.dpcg(A, lab, P.d, tol=1e-13)
+        assert _relerr(x1, tight.x) <= max(1e-7, 3 * _relerr(ref.x, tight.x))
     s.close()
