@@ -37,6 +37,7 @@ WORKLOAD = "lognormal-layered 256x256x128, point source, 4x4x4 subdomains x 2 le
 BYTES_ITER_FP32 = 60   # A: z, p_old, 3 faces, label, p_new  B: p, label, 3 faces, z r/w, xhat r/w
 BYTES_ITER_FP64 = 140  # same vectors and faces in FP64 + diag (A, B) and 1/diag (B)
 BYTES_OUTER = 152      # O1: x, xhat, b, faces, diag, label, r'  O2: r', label, faces, diag, x r/w, xhat r/w, 1/diag, z, p0, p1
+BYTES_ITER_BF16 = 52   # A: z, p_old, 3 BF16 faces, label, p_new  B: p, label, 3 BF16 faces, FP32 1/diag, z r/w, xhat r/w
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) over algorithmic
 # bytes of one launch of k_solve_tma<float, float, 8, 3, true, false>, from an
 # ncu capture of a 300-iteration launch on this workload; the traffic of a
@@ -112,7 +113,7 @@ def _dist():
     return replicas.dist_env()
 
 
-def cpu_baseline(P, A=None, lab=None, iters_full=None, sample_iters=40, threads=None):
+def cpu_baseline(P, A=None, lab=None, iters_full=None, sample_iters=40, threads=None, single_thread_iters=0):
     """Time the CPU oracle on a bounded sample: `sample_iters` deflated-CG
     iterations (plus its setup), scaled to the full iteration count."""
     import oracle
@@ -136,10 +137,91 @@ def cpu_baseline(P, A=None, lab=None, iters_full=None, sample_iters=40, threads=
     setup = max(0.0, (t2 - t1) - per_iter)
     full = iters_full if iters_full else r.iterations
     est_s = (t1 - t0) + setup + per_iter * full
-    return {"value": est_s * 1e3, "unit": "ms", "cores": oracle.max_threads(), "kind": "oracle",
-            "sample": f"oracle FP64 DPCG on the full workload: setup {setup:.1f} s, {its} timed iterations "
-                      f"({per_iter * 1e3:.0f} ms each), assembly/labels {t1 - t0:.1f} s, "
-                      f"scaled to {full} iterations"}
+    out = {"value": est_s * 1e3, "unit": "ms", "cores": oracle.max_threads(), "kind": "oracle",
+           "sample": f"oracle FP64 DPCG on the full workload: setup {setup:.1f} s, {its} timed iterations "
+                     f"({per_iter * 1e3:.0f} ms each), assembly/labels {t1 - t0:.1f} s, "
+                     f"scaled to {full} iterations"}
+    if single_thread_iters:
+        # the same iterations on one core (the oracle's plain loops)
+        nt = oracle.max_threads()
+        oracle.set_threads(1)
+        try:
+            t4 = time.perf_counter()
+            oracle.dpcg(A, lab, P.d, tol=P.tol, maxiter=1)
+            t5 = time.perf_counter()
+            oracle.dpcg(A, lab, P.d, tol=P.tol, maxiter=1 + single_thread_iters)
+            t6 = time.perf_counter()
+        finally:
+            oracle.set_threads(nt)
+        pi1 = max(0.0, (t6 - t5) - (t5 - t4)) / single_thread_iters
+        su1 = max(0.0, (t5 - t4) - pi1)
+        out["single_thread"] = {"value": ((t1 - t0) + su1 + pi1 * full) * 1e3, "unit": "ms", "cores": 1,
+                                "sample": f"{single_thread_iters} timed iterations ({pi1 * 1e3:.0f} ms each), "
+                                          f"setup {su1:.1f} s, scaled to {full} iterations"}
+    return out
+
+
+def bench_c2(sld, torch, reps=1):
+    """The 512x512x256 inclusion workload (67M cells, tilted lens/channel
+    inclusions at 1e-6 in a K = 1 background, >= 20 % of the volume,
+    8x8x8 subdomains x 3 levelsets: d = 1536): BF16 coefficients with an
+    FP32 per-cell inverse diagonal (with the refinement's forward-error test,
+    and with the residual test alone), FP32 inner, and plain FP64; each with
+    the algorithmic GB/s of its persistent kernel against the measured HBM
+    peak."""
+    from paper_1510_02148_gb300 import workloads as W
+    P, frac = W.inclusion_field()
+    Kd = torch.from_numpy(P.K.reshape(-1)).cuda()
+    t0 = time.perf_counter()
+    s = sld.System(Kd, None, P.bc_type, P.bc_value, shape=P.shape)
+    s.make_labels(P.S, P.tau, P.L)
+    s.build_deflation(P.d)
+    torch.cuda.synchronize()
+    setup_ms = (time.perf_counter() - t0) * 1e3
+    x = torch.empty(P.n, dtype=torch.float64, device="cuda")
+    peak, peak_kind = _peaks()
+    out = {"workload": f"inclusions 512x512x256 ({frac * 100:.1f} % at 1e-6), 8x8x8 subdomains x 3 levelsets "
+                       f"(d = {P.d}), tol 1e-9", "n": P.n, "d": P.d, "setup_ms": setup_ms}
+    forms = (("bf16", sld.BF16COEF_IR, 0.0, BYTES_ITER_BF16), ("bf16_residual_only", sld.BF16COEF_IR, -1.0, BYTES_ITER_BF16),
+             ("fp32_ir", sld.FP32_IR, 0.0, BYTES_ITER_FP32), ("fp64", sld.FP64, 0.0, BYTES_ITER_FP64))
+    for name, prec, fwd, bpc in forms:
+        s.solve(x=x, precision=prec, fwd_tol=fwd, maxiter=50, raise_on_error=False)  # warm-up (tensor maps, code)
+        ms = []
+        for _ in range(reps):
+            _, i = s.solve(x=x, precision=prec, fwd_tol=fwd)
+            ms.append(i.solve_ms)
+        kms = statistics.median(ms)
+        alg = P.n * (bpc * i.iterations + BYTES_OUTER * i.outer_steps)
+        ach = alg / (kms * 1e-3) / 1e9
+        out[name] = {"ms": kms, "iterations": i.iterations, "outer_steps": i.outer_steps,
+                     "true_relres": i.true_relres, "fwd_err_estimate": i.fwd_err_estimate,
+                     "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                                  "bytes_per_cell_iter": bpc, "peak_kind": peak_kind}}
+    out["speedup_bf16_vs_fp64"] = out["fp64"]["ms"] / out["bf16"]["ms"]
+    out["speedup_fp32_vs_fp64"] = out["fp64"]["ms"] / out["fp32_ir"]["ms"]
+    s.close()
+    return out
+
+
+def bench_c0(sld, torch, reps=5):
+    """The 32^3 layered sandwich (8 z-layers 1 / 1e-6, Dirichlet x-faces,
+    2x2x2 subdomains x 2 levelsets: d = 16): L2-resident and barrier-bound,
+    reported as time only."""
+    from paper_1510_02148_gb300 import workloads as W
+    P = W.layered_sandwich()
+    s = sld.from_problem(P)
+    x = torch.empty(P.n, dtype=torch.float64, device="cuda")
+    out = {"workload": "layered sandwich 32^3, 2x2x2 subdomains x 2 levelsets (d = 16), tol 1e-9"}
+    for name, prec in (("fp64", sld.FP64), ("fp32_ir", sld.FP32_IR), ("bf16", sld.BF16COEF_IR)):
+        s.solve(x=x, precision=prec)
+        ms = []
+        for _ in range(reps):
+            _, i = s.solve(x=x, precision=prec)
+            ms.append(i.solve_ms)
+        out[name] = {"ms": statistics.median(ms), "iterations": i.iterations, "outer_steps": i.outer_steps,
+                     "true_relres": i.true_relres}
+    s.close()
+    return out
 
 
 def gmres_bytes(n, m, its, cycles, deflated):
@@ -364,6 +446,17 @@ def run_reference(args):
         if k >= args.warmup:
             vals.append(cb["value"])
     v = statistics.median(vals)
+    full = None
+    if args.ref_full_solve:
+        # one whole oracle solve, timed, beside the per-step samples: checks
+        # the extrapolation and the recorded iteration count
+        t0 = time.perf_counter()
+        r = oracle.dpcg(A, lab, P.d, tol=P.tol)
+        full_ms = (time.perf_counter() - t0) * 1e3
+        full = {"ms": full_ms, "iterations": r.iterations, "true_relres": r.true_relres,
+                "recorded_iterations": full_iters,
+                "iterations_match_record": full_iters is None or r.iterations == full_iters,
+                "extrapolated_over_measured": v / full_ms}
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -371,6 +464,8 @@ def run_reference(args):
             "cpu_baseline": {"kind": "oracle", "cores": cb["cores"], "sample": cb["sample"], "value": v,
                              "unit": "ms"},
             "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    if full is not None:
+        line["full_solve_measured"] = full
     print(json.dumps(line), flush=True)
     return 0
 
@@ -384,9 +479,12 @@ def profile_solve(args):
     _build.build()
     sld.load()
     shape = tuple(args.shape) if args.shape else (256, 256, 128)
-    P = W.lognormal_point_source(*shape, seed=1)
-    s = sld.System(torch.from_numpy(P.K.reshape(-1)).cuda(), torch.from_numpy(P.q.reshape(-1)).cuda(),
-                   P.bc_type, P.bc_value, shape=P.shape)
+    if args.profile_workload == "inclusions":
+        P = W.inclusion_field(*shape, S=(8, 8, 8), a_range=tuple(max(4, int(a * shape[0] / 512)) for a in (16, 96)))[0]
+    else:
+        P = W.lognormal_point_source(*shape, seed=1)
+    q = None if P.q is None else torch.from_numpy(P.q.reshape(-1)).cuda()
+    s = sld.System(torch.from_numpy(P.K.reshape(-1)).cuda(), q, P.bc_type, P.bc_value, shape=P.shape)
     s.make_labels(P.S, P.tau, P.L)
     s.build_deflation(P.d)
     x = torch.empty(P.n, dtype=torch.float64, device="cuda")
@@ -413,11 +511,17 @@ def main():
     ap.add_argument("--no-gmres", action="store_true")
     ap.add_argument("--no-auto-labels", action="store_true")
     ap.add_argument("--no-spe10", action="store_true")
+    ap.add_argument("--no-c2", action="store_true")
+    ap.add_argument("--no-c0", action="store_true")
+    ap.add_argument("--ref-full-solve", type=int, default=1,
+                    help="reference arm: also time one full oracle solve (1) or not (0)")
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--profile-solve", choices=["fp64", "fp32_ir", "bf16"], default=None,
                     help="set up the workload and run one solve (for profiler captures); no timing line")
     ap.add_argument("--maxiter", type=int, default=0, help="with --profile-solve: inner iteration cap")
     ap.add_argument("--shape", type=int, nargs=3, default=None, help="with --profile-solve: grid nx ny nz")
+    ap.add_argument("--profile-workload", choices=["lognormal", "inclusions"], default="lognormal",
+                    help="with --profile-solve: the lognormal point-source field or the inclusion field")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -480,7 +584,7 @@ def main():
     qh = torch.from_numpy(P.q.reshape(-1)).pin_memory()
     xh = torch.empty(P.n, dtype=torch.float64).pin_memory()
     e2e = []
-    for k in range(2):
+    for k in range(3):
         barrier()
         t = time.perf_counter()
         s2 = sld.System(Kh, qh, P.bc_type, P.bc_value, stream=stream.cuda_stream, shape=P.shape)
@@ -490,7 +594,7 @@ def main():
         barrier()
         e2e.append((time.perf_counter() - t) * 1e3)
         s2.close()
-    e2e_ms = min(e2e)
+    e2e_ms = statistics.median(e2e)
 
     line = {
         "metric": METRIC, "value": ms_step, "unit": "ms", "n_gpus": world, "steps": args.steps,
@@ -532,8 +636,12 @@ def main():
         leg("auto_labels", bench_auto_labels, sld, torch, P, x)
     if not args.no_spe10:
         leg("spe10_like", bench_spe10, sld, torch)
+    if not args.no_c2:
+        leg("c2_inclusions", bench_c2, sld, torch)
+    if not args.no_c0:
+        leg("c0_sandwich", bench_c0, sld, torch)
     if rank == 0 and not args.no_cpu:
-        leg("cpu_baseline", cpu_baseline, P, None, None, fp64[-1].iterations, 30)
+        leg("cpu_baseline", cpu_baseline, P, None, None, fp64[-1].iterations, 30, None, 4)
     s.close()
     if rank == 0:
         print(json.dumps(line), flush=True)

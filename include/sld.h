@@ -102,10 +102,19 @@ typedef struct {
                              10x, not the 0.3 tol floor), reached it, and changed
                              x by at most fwd_tol * ||x||: that change estimates
                              the error of the previous iterate, which the step
-                             does not increase.  0 = 100 * tol (the default);
-                             < 0 = off (the residual test alone, fewer steps on
-                             high-contrast fields, larger error in the directions
-                             of the smallest eigenvalues). */
+                             does not increase.  A step that cut the residual
+                             and shrank the correction each at least 1e3-fold
+                             is also accepted when |d_k|^2 / |d_{k-1}| (its
+                             error at that contraction) is <= fwd_tol / 10.
+                             Where the inner precision cannot
+                             resolve the slowest modes the corrections stop
+                             shrinking: the test then gives up (the residual test
+                             stands) once a verified correction fails to halve
+                             the previous one, or after 4 steps past the residual
+                             test.  0 = 100 * tol (the default); < 0 = off (the
+                             residual test alone: fewer steps on high-contrast
+                             fields, larger error along the smallest
+                             eigenvalues). */
 } sld_options;
 
 typedef struct {
@@ -116,9 +125,10 @@ typedef struct {
   double solve_ms;         /* device time of the persistent solve kernel (CUDA events) */
   int kernel_path;         /* 1: TMA-pipelined sweeps (nx % 8 == 0), 0: register/shuffle sweeps,
                               2: batched launch (register/shuffle sweeps) */
-  double fwd_err_estimate; /* mixed modes: |d| / |x| of the last step that passed the
-                              forward-error test's conditions (see fwd_tol); -1 = none
-                              (SLD_FP64, or the test off and never met) */
+  double fwd_err_estimate; /* mixed modes: the forward-error test's last estimate (see
+                              fwd_tol): |d| / |x| of a verified step, or the
+                              contraction estimate of an accepted fast step; -1 =
+                              none (SLD_FP64, or the test off and never met) */
 } sld_result;
 
 /* Fill *o with the defaults listed above. */

@@ -740,10 +740,13 @@ sld_status sld_batch_create(sld_system* systems, int count, const sld_options* o
   struct Cand { int per; double expo; int cx; };
   std::vector<Cand> cands;
   for (int cx : (all4 ? std::vector<int>{1, 4} : std::vector<int>{1}))
-    for (double ex : {1.0, 4.0 / 3.0}) cands.push_back({o.ctas_per_sm, ex, cx});
-  if (o.ctas_per_sm > 0) cands = {{o.ctas_per_sm, 4.0 / 3.0, all4 ? 4 : 1}};
+    cands.push_back({o.ctas_per_sm, 1.0, cx});
+  if (o.ctas_per_sm > 0) cands = {{o.ctas_per_sm, 1.0, all4 ? 4 : 1}};
+  // the trial solves also give the iterations of the measured-iterations plan
+  const bool time_trials = cands.size() > 1 || o.ctas_per_sm <= 0;
   std::string times;
   float best_ms = 0.f;
+  std::vector<double> last_teams(count, 1.0);  // the teams of the last timed launch
   for (size_t c = 0; c < cands.size(); ++c) {
     sld::BatchPlan trial;
     std::string msg;
@@ -760,7 +763,7 @@ sld_status sld_batch_create(sld_system* systems, int count, const sld_options* o
       continue;
     }
     float ms = 0.f;
-    if (cands.size() > 1) {  // time one full batched solve with this shape
+    if (time_trials) {  // time one full batched solve with this shape
       std::swap(bt->plan, trial);
       sld_status ls = batch_launch(bt, &ms);
       std::swap(bt->plan, trial);
@@ -772,6 +775,7 @@ sld_status sld_batch_create(sld_system* systems, int count, const sld_options* o
       times += " [cx " + std::to_string(cands[c].cx) + ", expo " + std::to_string(cands[c].expo).substr(0, 4) +
                ": " + std::to_string(ms).substr(0, 7) + " ms]";
     }
+    for (int k = 0; k < count; ++k) last_teams[k] = trial.teams[k];
     if (!bt->plan.exec || ms < best_ms) {
       sld::batch_free(&bt->plan);
       bt->plan = trial;
@@ -780,40 +784,40 @@ sld_status sld_batch_create(sld_system* systems, int count, const sld_options* o
       sld::batch_free(&trial);
     }
   }
-  // one more candidate: teams proportional to each system's measured work
-  // (cells x iterations of the trial solves), the same launch shape
-  if (cands.size() > 1 && bt->plan.exec) {
+  // two more candidates: teams rebalanced from the CTA-time each system took
+  // in the last timed launch (its team's CTAs x its time in the kernel), the
+  // same launch shape; the second from the first's measurement
+  for (int round = 0; round < 2 && o.ctas_per_sm <= 0 && bt->plan.exec; ++round) {
     std::vector<double> wk(count);
     bool okw = true;
     for (int k = 0; k < count && okw; ++k) {
       double out[sld::kOutCount];
-      sld_system s = systems[k];
-      okw = cudaMemcpy(out, s->out, sizeof(out), cudaMemcpyDeviceToHost) == cudaSuccess;
-      const double its = out[sld::kOutIters] + 3.0 * out[sld::kOutOuter];
-      wk[k] = (double)s->g.n * std::max(its, 1.0);
+      okw = cudaMemcpy(out, systems[k]->out, sizeof(out), cudaMemcpyDeviceToHost) == cudaSuccess;
+      wk[k] = std::max(out[sld::kOutEndNs] - out[sld::kOutStartNs], 1.0) * last_teams[k];
     }
     sld::BatchPlan trial;
     std::string msg;
-    if (okw && sld::batch_build(bt->sys.data(), count, o, bt->plan.per_sm, 1.0, wk.data(), bt->plan.cx, bt->stream,
-                                &trial, &msg) == SLD_OK) {
-      float ms = 0.f;
-      std::swap(bt->plan, trial);
-      sld_status ls = batch_launch(bt, &ms);
-      std::swap(bt->plan, trial);
-      if (ls != SLD_OK) {
-        sld::batch_free(&trial);
-        sld_batch_destroy(bt);
-        return ls;
-      }
-      times += " [measured work: " + std::to_string(ms).substr(0, 7) + " ms]";
-      if (ms < best_ms) {
-        sld::batch_free(&bt->plan);
-        bt->plan = trial;
-        bt->plan.expo = -1.0;  // marks the measured-work plan
-        best_ms = ms;
-      } else {
-        sld::batch_free(&trial);
-      }
+    if (!okw || sld::batch_build(bt->sys.data(), count, o, bt->plan.per_sm, 1.0, wk.data(), bt->plan.cx, bt->stream,
+                                 &trial, &msg) != SLD_OK) {
+      sld::batch_free(&trial);
+      break;
+    }
+    float ms = 0.f;
+    std::swap(bt->plan, trial);
+    sld_status ls = batch_launch(bt, &ms);
+    std::swap(bt->plan, trial);
+    if (ls != SLD_OK) {
+      sld::batch_free(&trial);
+      sld_batch_destroy(bt);
+      return ls;
+    }
+    times += " [rebalanced " + std::to_string(round + 1) + ": " + std::to_string(ms).substr(0, 7) + " ms]";
+    for (int k = 0; k < count; ++k) last_teams[k] = trial.teams[k];
+    if (ms < best_ms) {
+      sld::batch_free(&bt->plan);
+      bt->plan = trial;
+      bt->plan.expo = -1.0;  // marks a rebalanced plan
+      best_ms = ms;
     } else {
       sld::batch_free(&trial);
     }
@@ -821,7 +825,7 @@ sld_status sld_batch_create(sld_system* systems, int count, const sld_options* o
   const sld::BatchPlan& p = bt->plan;
   bt->desc = "systems " + std::to_string(count) + ", CTAs " + std::to_string(p.G) + " (" + std::to_string(p.per_sm) +
              " per SM), " + (p.tma ? std::string("TMA sweeps, 64x8 tiles") : "cells per lane " + std::to_string(p.cx)) +
-             ", teams by " + (p.expo < 0 ? std::string("measured work") : "n^" + std::to_string(p.expo).substr(0, 4)) +
+             ", teams by " + (p.expo < 0 ? std::string("measured CTA-time") : "n^" + std::to_string(p.expo).substr(0, 4)) +
              ":";
   for (int k = 0; k < count; ++k) bt->desc += " " + std::to_string(p.teams[k]);
   if (!times.empty()) bt->desc += "; autotune:" + times;
@@ -852,6 +856,28 @@ sld_status sld_batch_solve(sld_batch bt, const double* const* b, double* const* 
     if (sk != SLD_OK && worst == SLD_OK) {
       worst = sk;
       first_msg = "system " + std::to_string(k) + ": " + g_last_error;
+    }
+  }
+  // per-team span of the last launch, relative to the earliest team start
+  {
+    std::vector<double> t0(count), t1(count);
+    bool ok = true;
+    for (int k = 0; k < count && ok; ++k) {
+      double out[sld::kOutCount];
+      ok = cudaMemcpy(out, bt->sys[k]->out, sizeof(out), cudaMemcpyDeviceToHost) == cudaSuccess;
+      t0[k] = out[sld::kOutStartNs];
+      t1[k] = out[sld::kOutEndNs];
+    }
+    if (ok && count > 0) {
+      const double base = *std::min_element(t0.begin(), t0.end());
+      std::string d = bt->desc.substr(0, bt->desc.find("; last solve:"));
+      d += "; last solve: team end ms:";
+      char buf[32];
+      for (int k = 0; k < count; ++k) {
+        std::snprintf(buf, sizeof(buf), " %.1f", (t1[k] - base) * 1e-6);
+        d += buf;
+      }
+      bt->desc = d;
     }
   }
   if (worst != SLD_OK) return fail(worst, first_msg);

@@ -88,9 +88,10 @@ struct SolveArgs {
 
 enum {
   kOutIters = 0, kOutOuter, kOutRR, kOutBB, kOutStatus, kOutRecRR, kOutFwd,
+  kOutStartNs, kOutEndNs,  // the team's first and last moment in the kernel (%globaltimer, ns)
   // refinement trace (mixed forms): for outer step k < kTraceSteps, the
   // squared norm of its correction at kOutTrace + 2k, its residual at +2k+1
-  kOutTrace = 8, kTraceSteps = 16, kOutCount = kOutTrace + 2 * kTraceSteps
+  kOutTrace = 10, kTraceSteps = 16, kOutCount = kOutTrace + 2 * kTraceSteps
 };
 
 }  // namespace sld
@@ -174,8 +175,13 @@ int tma_batch_occupancy(bool wacc, size_t smem);
 void tma_batch_tiles(SolveArgs* a);
 size_t tma_maps_bytes();
 bool tma_batch_maps(const SolveArgs& a, void* out);  // host memory, tma_maps_bytes() bytes
+// h_args (count systems, host): when count <= tma_batch_param_max(), every
+// system's arguments go into one kernel parameter; else the kernel copies
+// its system's arguments from d_args into shared memory
 cudaError_t tma_batch_launch(int G, size_t smem, unsigned args_off, bool wacc, const SolveArgs* d_args,
-                             const void* d_maps, const int* d_cta, cudaStream_t st);
+                             const SolveArgs* h_args, int count, const void* d_maps, const int* d_cta,
+                             cudaStream_t st);
+int tma_batch_param_max();
 // sld_solve_tma_learned.cu (extra dense deflation columns)
 int launch_solve_tma_learned(sld_system s, SolveArgs& a, const sld_options& o, float* ms, std::string* msg);
 // sld_api.cu: the thread-local message returned by sld_last_error()
@@ -211,13 +217,15 @@ struct BatchPlan {
   SolveArgs* d_args = nullptr;
   int* d_cta = nullptr;
   double* d_gacc = nullptr;  // global per-warp label-sum rows (dmax > kWarpAccMaxD)
+  SolveArgs* h_args = nullptr;  // host copy of the systems' arguments (new[], count)
   cudaStream_t stream = nullptr;  // the batch's own stream (capture and launch), not owned here
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int teams[4096];
 };
-// weights: team shares (count values), or nullptr for n^expo
-int batch_build(sld_system* sys, int count, const sld_options& o, int per_sm, double expo, const double* weights,
+// cost: measured CTA-time per system (count values; teams by min-max of
+// cost / team), or nullptr for teams proportional to n^expo
+int batch_build(sld_system* sys, int count, const sld_options& o, int per_sm, double expo, const double* cost,
                 int cx, cudaStream_t stream, BatchPlan* plan, std::string* msg);
 void batch_free(BatchPlan* plan);
 }  // namespace sld

@@ -878,7 +878,8 @@ int batch_capture(sld_system s0, BatchPlan* p, sld_system* sys, std::string* msg
   }
   cudaError_t el;
   if (p->tma) {
-    el = tma_batch_launch(p->G, p->smem, p->args_off, p->wacc, p->d_args, p->d_maps, p->d_cta, st);
+    el = tma_batch_launch(p->G, p->smem, p->args_off, p->wacc, p->d_args, p->h_args, p->count, p->d_maps, p->d_cta,
+                          st);
   } else {
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(p->G);
@@ -930,19 +931,24 @@ void batch_free(BatchPlan* p) {
   if (p->d_cta) cudaFree(p->d_cta);
   if (p->d_maps) cudaFree(p->d_maps);
   if (p->d_gacc) cudaFree(p->d_gacc);
+  delete[] p->h_args;
   p->d_maps = nullptr;
   p->d_gacc = nullptr;
+  p->h_args = nullptr;
   p->exec = nullptr;
   p->graph = nullptr;
   p->d_args = nullptr;
   p->d_cta = nullptr;
 }
 
-// Teams: system k gets a share of the CTAs proportional to its weight --
-// n_k^expo by default (work per iteration grows with n, the iteration count
-// roughly with the side), or the caller's (measured work) -- at least one
-// CTA, at most one per plane tile and per partial-sum row.
-int batch_build(sld_system* sys, int count, const sld_options& o, int per_sm, double expo, const double* weights,
+// Teams: at least one CTA per system, at most one per plane tile and per
+// partial-sum row.  Without a measurement, system k's share is proportional
+// to n_k^expo.  With one (cost: the CTA-time each system took in an earlier
+// launch, its team's CTAs x its time in the kernel), the CTAs are dealt out
+// to minimise the slowest system's modelled time T_k(t) = cost_k / t:
+// every system starts with one CTA and each further CTA goes to the
+// currently slowest system (optimal for these decreasing convex times).
+int batch_build(sld_system* sys, int count, const sld_options& o, int per_sm, double expo, const double* cost,
                 int cx, cudaStream_t stream, BatchPlan* p, std::string* msg) {
   sld_system s0 = sys[0];
   p->stream = stream;
@@ -997,34 +1003,53 @@ int batch_build(sld_system* sys, int count, const sld_options& o, int per_sm, do
       a.ntiles = (int64_t)a.ntx * a.nty * a.g.nz;
     }
     cap[k] = (int)std::min<int64_t>(std::min<int64_t>(a.ntiles, sys[k]->part_rows), G);
-    w[k] = weights ? std::max(weights[k], 1e-30) : std::pow((double)a.g.n, expo);
+    w[k] = std::pow((double)a.g.n, expo);
     wsum += w[k];
   }
   int used = 0;
-  for (int k = 0; k < count; ++k) {
-    ideal[k] = G * w[k] / wsum;
-    p->teams[k] = std::max(1, std::min(cap[k], (int)ideal[k]));
-    used += p->teams[k];
-  }
-  while (used > G) {  // give back from the largest teams
-    int j = 0;
-    for (int k = 1; k < count; ++k)
-      if (p->teams[k] > p->teams[j]) j = k;
-    if (p->teams[j] <= 1) break;
-    --p->teams[j];
-    --used;
-  }
-  while (used < G) {  // hand out the rest where the share is most short
-    int j = -1;
-    double best = -1e300;
-    for (int k = 0; k < count; ++k)
-      if (p->teams[k] < cap[k] && ideal[k] - p->teams[k] > best) {
-        best = ideal[k] - p->teams[k];
-        j = k;
-      }
-    if (j < 0) break;
-    ++p->teams[j];
-    ++used;
+  if (cost) {  // min-max over the modelled times, greedy
+    for (int k = 0; k < count; ++k) p->teams[k] = 1;
+    used = count;
+    auto T = [&](int k, int t) { return std::max(cost[k], 1e-9) / t; };
+    std::vector<std::pair<double, int>> heap;
+    for (int k = 0; k < count; ++k) heap.push_back({T(k, 1), k});
+    std::make_heap(heap.begin(), heap.end());
+    while (used < G && !heap.empty()) {
+      std::pop_heap(heap.begin(), heap.end());
+      const int k = heap.back().second;
+      heap.pop_back();
+      if (p->teams[k] >= cap[k]) break;  // the slowest system cannot be sped up: stop
+      ++p->teams[k];
+      ++used;
+      heap.push_back({T(k, p->teams[k]), k});
+      std::push_heap(heap.begin(), heap.end());
+    }
+  } else {
+    for (int k = 0; k < count; ++k) {
+      ideal[k] = G * w[k] / wsum;
+      p->teams[k] = std::max(1, std::min(cap[k], (int)ideal[k]));
+      used += p->teams[k];
+    }
+    while (used > G) {  // give back from the largest teams
+      int j = 0;
+      for (int k = 1; k < count; ++k)
+        if (p->teams[k] > p->teams[j]) j = k;
+      if (p->teams[j] <= 1) break;
+      --p->teams[j];
+      --used;
+    }
+    while (used < G) {  // hand out the rest where the share is most short
+      int j = -1;
+      double best = -1e300;
+      for (int k = 0; k < count; ++k)
+        if (p->teams[k] < cap[k] && ideal[k] - p->teams[k] > best) {
+          best = ideal[k] - p->teams[k];
+          j = k;
+        }
+      if (j < 0) break;
+      ++p->teams[j];
+      ++used;
+    }
   }
   p->G = used;
   std::vector<int> cta_sys;
@@ -1055,6 +1080,8 @@ int batch_build(sld_system* sys, int count, const sld_options& o, int per_sm, do
     e = cudaMalloc(&p->d_maps, maps.size());
     if (e == cudaSuccess) e = cudaMemcpy(p->d_maps, maps.data(), maps.size(), cudaMemcpyHostToDevice);
   }
+  p->h_args = new SolveArgs[count];
+  std::memcpy(p->h_args, args.data(), sizeof(SolveArgs) * count);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(p->d_args, args.data(), sizeof(SolveArgs) * count, cudaMemcpyHostToDevice, stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(p->d_cta, cta_sys.data(), sizeof(int) * used, cudaMemcpyHostToDevice, stream);

@@ -1,5 +1,9 @@
 // sld_solve_tma.cu -- instantiations of the TMA-pipelined persistent solve
 // for label deflation alone (extra dense columns: sld_solve_tma_learned.cu).
+#include <algorithm>
+#include <cstring>
+#include <memory>
+
 #include "sld_solve_tma.cuh"
 
 namespace sld {
@@ -65,13 +69,22 @@ unsigned tma_batch_args_off(int dmax, bool wacc) {
 size_t tma_batch_smem(int dmax, bool wacc) { return tma_batch_args_off(dmax, wacc) + sizeof(SolveArgs); }
 
 int tma_batch_occupancy(bool wacc, size_t smem) {
-  const void* kern = wacc ? (const void*)k_solve_tma_batch<float, float, kBTY, 3, true>
-                          : (const void*)k_solve_tma_batch<float, float, kBTY, 3, false>;
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  int per = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 16 * kBTY, smem);
-  return per;
+  // both kernels (arguments in shared memory / in the parameter space) must fit
+  const void* kerns[2] = {wacc ? (const void*)k_solve_tma_batch<float, float, kBTY, 3, true>
+                               : (const void*)k_solve_tma_batch<float, float, kBTY, 3, false>,
+                          wacc ? (const void*)k_solve_tma_batch_p<float, float, kBTY, 3, true>
+                               : (const void*)k_solve_tma_batch_p<float, float, kBTY, 3, false>};
+  int best = 1 << 30;
+  for (const void* kern : kerns) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 16 * kBTY, smem);
+    best = std::min(best, per);
+  }
+  return best;
 }
+
+int tma_batch_param_max() { return kBatchParamMax; }
 
 void tma_batch_tiles(SolveArgs* a) {
   a->ntx = (a->g.nx + kTX - 1) / kTX;
@@ -84,7 +97,8 @@ size_t tma_maps_bytes() { return sizeof(Maps); }
 bool tma_batch_maps(const SolveArgs& a, void* out) { return build_maps<float, float, kBTY>(a, static_cast<Maps*>(out)); }
 
 cudaError_t tma_batch_launch(int G, size_t smem, unsigned args_off, bool wacc, const SolveArgs* d_args,
-                             const void* d_maps, const int* d_cta, cudaStream_t st) {
+                             const SolveArgs* h_args, int count, const void* d_maps, const int* d_cta,
+                             cudaStream_t st) {
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(G);
   cfg.blockDim = dim3(16 * kBTY);
@@ -96,6 +110,14 @@ cudaError_t tma_batch_launch(int G, size_t smem, unsigned args_off, bool wacc, c
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   const Maps* mp = static_cast<const Maps*>(d_maps);
+  if (h_args && count <= kBatchParamMax) {
+    // host staging of the parameter: the launch (or the graph capture) copies it
+    auto P = std::make_unique<BatchParam>();
+    std::memset(P.get(), 0, sizeof(BatchParam));
+    std::memcpy(P->a, h_args, sizeof(SolveArgs) * count);
+    if (wacc) return cudaLaunchKernelEx(&cfg, k_solve_tma_batch_p<float, float, kBTY, 3, true>, *P, mp, d_cta);
+    return cudaLaunchKernelEx(&cfg, k_solve_tma_batch_p<float, float, kBTY, 3, false>, *P, mp, d_cta);
+  }
   if (wacc) return cudaLaunchKernelEx(&cfg, k_solve_tma_batch<float, float, kBTY, 3, true>, d_args, mp, d_cta, args_off);
   return cudaLaunchKernelEx(&cfg, k_solve_tma_batch<float, float, kBTY, 3, false>, d_args, mp, d_cta, args_off);
 }

@@ -715,6 +715,25 @@ __global__ void __launch_bounds__(16 * TY, tma_min_ctas<T, TY>()) k_solve_tma_ba
   tma_body<T, F, TY, S, WACC, false>(*as, maps[k], as->ntx, smem_raw);
 }
 
+// Batched solve with every system's arguments in one kernel parameter (up to
+// kBatchParamMax systems): a CTA reads its system's arguments from the
+// constant bank like the single solve does, instead of from a shared-memory
+// copy that the compiler must reload after every shared-memory store.
+constexpr int kBatchParamMax = 72;  // 72 x sizeof(SolveArgs) fits the 32 KB parameter space
+struct BatchParam {
+  SolveArgs a[kBatchParamMax];
+};
+
+template <typename T, typename F, int TY, int S, bool WACC>
+__global__ void __launch_bounds__(16 * TY, tma_min_ctas<T, TY>())
+    k_solve_tma_batch_p(const __grid_constant__ BatchParam P, const Maps* __restrict__ maps,
+                        const int* __restrict__ cta_sys) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int k = cta_sys[blockIdx.x];
+  const SolveArgs& a = P.a[k];
+  tma_body<T, F, TY, S, WACC, false>(a, maps[k], a.ntx, smem_raw);
+}
+
 // ---------------------------------------------------------------------------
 // Host side: tensor maps and the launch.
 // ---------------------------------------------------------------------------
