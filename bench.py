@@ -388,10 +388,8 @@ def bench_learned(sld, torch, nfields=4):
         _, f64 = s.solve(x=x, precision=sld.FP64)
         s.solve(x=x, precision=sld.FP32_IR)
         _, f32 = s.solve(x=x, precision=sld.FP32_IR)
-        Y = torch.empty((P.n, 8), dtype=torch.float32, device="cuda")
         t0 = time.perf_counter()
-        net.forward(torch.from_numpy(P.K.reshape(-1)).cuda(), out=Y)
-        s.build_deflation(P.d, Zextra=Y)
+        net.infer(s)  # sld_learned_infer: network on the system's K, columns appended to its labels
         torch.cuda.synchronize()
         setup_ms = (time.perf_counter() - t0) * 1e3
         ku = s.deflation_info()[2]

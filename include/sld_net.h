@@ -84,6 +84,56 @@ sld_status sld_net_adam(sld_net net, float lr, float beta1, float beta2, float e
 
 void sld_net_destroy(sld_net net);
 
+/* ---------------------------------------------------------------------- */
+/* Training and use of the learned deflation vectors as single calls.      */
+/* ---------------------------------------------------------------------- */
+
+typedef struct {
+  int epochs;         /* passes over the training fields (default 12) */
+  float lr;           /* Adam step size of the first epochs (default 2e-3) */
+  float lr_decay;     /* factor applied every decay_every epochs (default 0.5) */
+  int decay_every;    /* 0 = max(1, epochs / 3) (the default) */
+  float beta1, beta2, eps;  /* Adam (defaults 0.9, 0.999, 1e-8) */
+  uint64_t seed;      /* order of the fields in each epoch (default 0) */
+} sld_train_options;
+
+/* Fill *o with the defaults listed above. */
+void sld_default_train_options(sld_train_options* o);
+
+/*
+ * Train the network on nfields fields: for each epoch, the fields in a
+ * random order (Fisher-Yates with the SplitMix64 generator seeded by
+ * seed + epoch); for each field one forward pass on K[i], the subspace loss
+ * against the targets V[i] (n x m FP32, as made by sld_lanczos_eigvecs) with
+ * the weights D[i] (diag A, n FP64) and its gradients, and one Adam step at
+ * lr * lr_decay^(epoch / decay_every) (step count running over all epochs).
+ * The network keeps the trained parameters (read them with
+ * sld_net_get_params).  The targets are the eigenvectors deflation should
+ * remove (Section 3.1); the network stands in for their per-system
+ * computation, which the paper finds too costly (Section 3.2.1).
+ *   K, V, D: arrays of nfields pointers (host or device each).
+ *   epoch_loss: epochs values (host) or NULL: the mean loss of each epoch.
+ * Errors: SLD_ERR_INVALID_ARG (NULL arrays, nfields < 1, m out of 1..8,
+ * options out of range), and those of the per-step calls.
+ */
+sld_status sld_learned_train(sld_net net, int nfields, const double* const* K, const float* const* V, int m,
+                             const double* const* D, const sld_train_options* o, double* epoch_loss);
+
+/*
+ * The learned deflation of a system: the network's 8 vectors for the
+ * system's own permeability (the K given to sld_build_system), appended to
+ * its subspace-levelset labels of the last sld_make_labels /
+ * sld_make_labels_cc call, as sld_build_deflation(s, NULL, d, Y, 8,
+ * SLD_ZEXTRA_F32) builds it (Def. 3.1 with Z = [Z_labels, Y]); if the
+ * columns fail that call's pivot test, the label deflation alone is built
+ * (sld_deflation_info reports it).  The network's grid must be the
+ * system's.
+ *   Zextra_out: n x 8 FP32 (host or device) or NULL: a copy of the vectors.
+ * Errors: SLD_ERR_INVALID_ARG (grid mismatch), SLD_ERR_STATE (no labels
+ * made), and those of sld_net_forward and sld_build_deflation.
+ */
+sld_status sld_learned_infer(sld_net net, sld_system s, float* Zextra_out);
+
 /*
  * Training targets: the k eigenpairs of the smallest eigenvalues of the
  * label-deflated, Jacobi-preconditioned operator M^{-1} P A of a built

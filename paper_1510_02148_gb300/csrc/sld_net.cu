@@ -795,6 +795,78 @@ sld_status sld_net_adam(sld_net net, float lr, float beta1, float beta2, float e
   return e == cudaSuccess ? SLD_OK : ncuda(e, "adam");
 }
 
+void sld_default_train_options(sld_train_options* o) {
+  if (!o) return;
+  o->epochs = 12;
+  o->lr = 2e-3f;
+  o->lr_decay = 0.5f;
+  o->decay_every = 0;
+  o->beta1 = 0.9f;
+  o->beta2 = 0.999f;
+  o->eps = 1e-8f;
+  o->seed = 0;
+}
+
+sld_status sld_learned_train(sld_net net, int nfields, const double* const* K, const float* const* V, int m,
+                             const double* const* D, const sld_train_options* opt, double* epoch_loss) {
+  sld::set_last_error("");
+  if (!net || !K || !V || !D) return nfail(SLD_ERR_INVALID_ARG, "NULL argument");
+  if (nfields < 1) return nfail(SLD_ERR_INVALID_ARG, "nfields must be >= 1");
+  if (m < 1 || m > 8) return nfail(SLD_ERR_INVALID_ARG, "m must be in [1, 8]");
+  sld_train_options o;
+  sld_default_train_options(&o);
+  if (opt) o = *opt;
+  if (o.epochs < 1 || !(o.lr > 0.f) || !(o.lr_decay > 0.f) || o.decay_every < 0 || !(o.beta1 >= 0.f) ||
+      !(o.beta1 < 1.f) || !(o.beta2 >= 0.f) || !(o.beta2 < 1.f) || !(o.eps > 0.f))
+    return nfail(SLD_ERR_INVALID_ARG, "training options out of range");
+  for (int i = 0; i < nfields; ++i)
+    if (!K[i] || !V[i] || !D[i]) return nfail(SLD_ERR_INVALID_ARG, "NULL field pointer");
+  const int every = o.decay_every > 0 ? o.decay_every : std::max(1, o.epochs / 3);
+  std::vector<int> order(nfields);
+  int step = 0;
+  for (int ep = 0; ep < o.epochs; ++ep) {
+    // Fisher-Yates with SplitMix64 (Steele, Lea and Flood 2014) seeded by seed + epoch
+    uint64_t st = o.seed + (uint64_t)ep;
+    auto next = [&st]() {
+      uint64_t z = (st += 0x9E3779B97F4A7C15ull);
+      z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+      z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+      return z ^ (z >> 31);
+    };
+    for (int i = 0; i < nfields; ++i) order[i] = i;
+    for (int i = nfields - 1; i > 0; --i) std::swap(order[i], order[(int)(next() % (uint64_t)(i + 1))]);
+    const float lr = o.lr * std::pow(o.lr_decay, (float)(ep / every));
+    double sum = 0.0;
+    for (int i : order) {
+      sld_status r = sld_net_forward(net, K[i], nullptr);
+      double loss = 0.0;
+      if (r == SLD_OK) r = sld_net_loss_backward(net, V[i], m, D[i], &loss);
+      if (r == SLD_OK) r = sld_net_adam(net, lr, o.beta1, o.beta2, o.eps, ++step);
+      if (r != SLD_OK) return r;
+      sum += loss;
+    }
+    if (epoch_loss) epoch_loss[ep] = sum / nfields;
+  }
+  return SLD_OK;
+}
+
+sld_status sld_learned_infer(sld_net net, sld_system s, float* Zextra_out) {
+  sld::set_last_error("");
+  if (!net || !s) return nfail(SLD_ERR_INVALID_ARG, "NULL argument");
+  const Dims& d = net->d[0];
+  if (d.nx != s->g.nx || d.ny != s->g.ny || d.nz != s->g.nz)
+    return nfail(SLD_ERR_INVALID_ARG, "the network's grid is not the system's");
+  if (!s->label || s->have_labels_d < 1) return nfail(SLD_ERR_STATE, "make the system's labels first");
+  sld_status r = sld_net_forward(net, s->K, nullptr);  // the handle's own K (device)
+  if (r != SLD_OK) return r;
+  if (Zextra_out) {
+    cudaError_t e = cudaMemcpyAsync(Zextra_out, net->out, sizeof(float) * d.n * kOutC, cudaMemcpyDefault, net->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(net->stream);
+    if (e != cudaSuccess) return ncuda(e, "copy the learned vectors");
+  }
+  return sld_build_deflation(s, nullptr, s->have_labels_d, net->out, kOutC, SLD_ZEXTRA_F32);
+}
+
 void sld_net_destroy(sld_net net) {
   if (!net) return;
   cudaStreamSynchronize(net->stream);

@@ -78,25 +78,14 @@ def init_params(seed=0):
 
 
 def train(net, data, epochs, lr=2e-3, seed=0, log=None, lr_decay=0.5, decay_every=None):
-    """Adam on the subspace loss, one field per step, shuffled each epoch.
-    Returns the mean loss of each epoch."""
-    rng = np.random.default_rng(seed)
-    step = 0
-    hist = []
-    decay_every = decay_every or max(1, epochs // 3)
-    for ep in range(epochs):
-        lr_ep = lr * (lr_decay ** (ep // decay_every))
-        losses = []
-        for i in rng.permutation(len(data)):
-            smp = data[i]
-            net.forward(smp["K"], keep=True)
-            losses.append(net.loss_backward(smp["V"], smp["D"]))
-            step += 1
-            net.adam(lr_ep, step)
-        hist.append(float(np.mean(losses)))
-        if log:
-            log(f"epoch {ep}: mean loss {hist[-1]:.4f} (lr {lr_ep:.1e})")
-    return hist
+    """Adam on the subspace loss, one field per step, shuffled each epoch:
+    one sld_learned_train call.  Returns the mean loss of each epoch."""
+    hist = net.train([d["K"] for d in data], [d["V"] for d in data], [d["D"] for d in data], epochs=epochs,
+                     lr=lr, lr_decay=lr_decay, decay_every=decay_every or 0, seed=seed)
+    if log:
+        for ep, h in enumerate(hist):
+            log(f"epoch {ep}: mean loss {h:.4f}")
+    return [float(h) for h in hist]
 
 
 def evaluate(net, seeds, n, precision=sld.FP32_IR, tol=1e-9):
@@ -109,10 +98,8 @@ def evaluate(net, seeds, n, precision=sld.FP32_IR, tol=1e-9):
         x = torch.empty(P.n, dtype=torch.float64, device="cuda")
         s.solve(x=x, precision=precision, tol=tol)  # warm-up
         _, plain = s.solve(x=x, precision=precision, tol=tol)
-        Y = torch.empty((P.n, 8), dtype=torch.float32, device="cuda")
         t0 = time.perf_counter()
-        net.forward(torch.from_numpy(P.K.reshape(-1)).cuda(), out=Y)
-        s.build_deflation(P.d, Zextra=Y)
+        net.infer(s)  # network on the system's own K, columns appended to its labels
         torch.cuda.synchronize()
         setup_ms = (time.perf_counter() - t0) * 1e3
         _, ku = s.deflation_info()[1:]

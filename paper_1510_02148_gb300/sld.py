@@ -34,7 +34,8 @@ EXPORTED = ["sld_default_options", "sld_build_system", "sld_make_labels", "sld_b
             "sld_net_num_params", "sld_net_create", "sld_net_set_params", "sld_net_get_params",
             "sld_net_get_grads", "sld_net_forward", "sld_net_backward", "sld_net_loss_backward",
             "sld_net_adam", "sld_net_destroy", "sld_lanczos_eigvecs", "sld_solve_gmres",
-            "sld_make_labels_cc", "sld_harmonic_ritz", "sld_solve_rdgmres"]
+            "sld_make_labels_cc", "sld_harmonic_ritz", "sld_solve_rdgmres", "sld_default_train_options",
+            "sld_learned_train", "sld_learned_infer"]
 
 
 class SldError(RuntimeError):
@@ -61,6 +62,11 @@ class Result(C.Structure):
     _fields_ = [("iterations", C.c_int), ("outer_steps", C.c_int), ("true_relres", C.c_double),
                 ("recursive_relres", C.c_double), ("solve_ms", C.c_double), ("kernel_path", C.c_int),
                 ("fwd_err_estimate", C.c_double)]
+
+
+class TrainOptions(C.Structure):
+    _fields_ = [("epochs", C.c_int), ("lr", C.c_float), ("lr_decay", C.c_float), ("decay_every", C.c_int),
+                ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float), ("seed", C.c_uint64)]
 
 
 class GmresInfo(C.Structure):
@@ -115,6 +121,10 @@ def load(path: str = LIB_PATH):
         lib.sld_net_adam.argtypes = [P, C.c_float, C.c_float, C.c_float, C.c_float, C.c_int]
         lib.sld_net_destroy.argtypes = [P]
         lib.sld_net_destroy.restype = None
+        lib.sld_default_train_options.argtypes = [C.POINTER(TrainOptions)]
+        lib.sld_default_train_options.restype = None
+        lib.sld_learned_train.argtypes = [P, C.c_int, P, P, C.c_int, P, C.POINTER(TrainOptions), P]
+        lib.sld_learned_infer.argtypes = [P, P, P]
         lib.sld_lanczos_eigvecs.argtypes = [P, C.c_int, C.c_int, P, P, P]
         lib.sld_make_labels_cc.argtypes = [P, C.c_int, C.c_int, C.c_int, P, C.c_int, P, C.POINTER(C.c_int)]
         lib.sld_solve_rdgmres.argtypes = [P, P, C.c_int, C.c_int, C.c_double, C.c_int, P, C.POINTER(GmresInfo)]
@@ -456,6 +466,32 @@ class Net:
 
     def adam(self, lr, step, beta1=0.9, beta2=0.999, eps=1e-8):
         _check(load().sld_net_adam(self._h, float(lr), float(beta1), float(beta2), float(eps), int(step)))
+
+    def train(self, Ks, Vs, Ds, **opts):
+        """sld_learned_train over the fields (Ks[i] n FP64, Vs[i] n x m FP32,
+        Ds[i] n FP64; host or device each).  opts: fields of TrainOptions.
+        Returns the mean loss of each epoch."""
+        o = TrainOptions()
+        load().sld_default_train_options(C.byref(o))
+        for k, v in opts.items():
+            if not hasattr(o, k):
+                raise KeyError(k)
+            setattr(o, k, v)
+        nf = len(Ks)
+        m = int(Vs[0].shape[1])
+        kp = (C.c_void_p * nf)(*[_ptr(K, np.float64) for K in Ks])
+        vp = (C.c_void_p * nf)(*[_ptr(V, np.float32) for V in Vs])
+        dp = (C.c_void_p * nf)(*[_ptr(D, np.float64) for D in Ds])
+        hist = np.zeros(o.epochs)
+        _check(load().sld_learned_train(self._h, nf, kp, vp, m, dp, C.byref(o), hist.ctypes.data))
+        return hist
+
+    def infer(self, system, out=None):
+        """sld_learned_infer: the network's vectors for the system's own K,
+        appended to its labels (the deflation is rebuilt).  Returns `out`
+        (n x 8 FP32) if given."""
+        _check(load().sld_learned_infer(self._h, system._h, _ptr(out, np.float32) if out is not None else None))
+        return out
 
     def close(self):
         if self._h:

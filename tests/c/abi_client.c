@@ -43,6 +43,17 @@ int main(void) {
     CHECK(sld_harmonic_ritz(Hbar, 1, 1, Y, tre, tim) == SLD_ERR_INVALID_ARG);
   }
   CHECK(sld_net_num_params() > 0);
+  {
+    /* the learned-deflation calls: defaults, and argument checks before any device work */
+    sld_train_options t;
+    memset(&t, 0xff, sizeof t);
+    sld_default_train_options(&t);
+    CHECK(t.epochs == 12 && t.lr > 1.99e-3f && t.lr < 2.01e-3f && t.lr_decay == 0.5f && t.decay_every == 0);
+    CHECK(t.beta1 == 0.9f && t.beta2 > 0.998f && t.seed == 0);
+    CHECK(sld_learned_train(NULL, 1, NULL, NULL, 8, NULL, &t, NULL) == SLD_ERR_INVALID_ARG);
+    CHECK(sld_learned_infer(NULL, NULL, NULL) == SLD_ERR_INVALID_ARG);
+    CHECK(strlen(sld_last_error()) > 0);
+  }
   sld_destroy(NULL); /* ignored */
   printf("%s\n", fails ? "FAIL" : "OK");
   return fails ? 1 : 0;

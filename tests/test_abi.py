@@ -29,7 +29,8 @@ def test_header_declares_entry_points():
     names = _declared()
     for must in ("sld_build_system", "sld_make_labels", "sld_build_deflation", "sld_solve",
                  "sld_destroy", "sld_last_error", "sld_net_forward", "sld_net_loss_backward",
-                 "sld_lanczos_eigvecs", "sld_solve_gmres", "sld_make_labels_cc", "sld_harmonic_ritz", "sld_solve_rdgmres"):
+                 "sld_lanczos_eigvecs", "sld_solve_gmres", "sld_make_labels_cc", "sld_harmonic_ritz", "sld_solve_rdgmres",
+                 "sld_learned_train", "sld_learned_infer"):
         assert must in names
 
 

@@ -52,3 +52,105 @@ def test_learned_vectors_cut_iterations(env, oracle_mod):
     assert abs(info.iterations - ref.iterations) <= 2
     s.close()
     net.close()
+
+
+def _splitmix_order(n, seed):
+    """The field order sld_learned_train documents: Fisher-Yates with the
+    SplitMix64 generator (Steele, Lea and Flood 2014) seeded by seed + epoch."""
+    M = (1 << 64) - 1
+    st = seed & M
+    order = list(range(n))
+
+    def nxt():
+        nonlocal st
+        st = (st + 0x9E3779B97F4A7C15) & M
+        z = st
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & M
+        return z ^ (z >> 31)
+
+    for i in range(n - 1, 0, -1):
+        j = nxt() % (i + 1)
+        order[i], order[j] = order[j], order[i]
+    return order
+
+
+def test_learned_train_is_the_documented_loop(env):
+    """sld_learned_train in one call gives the parameters of the per-step
+    calls (forward, loss and gradient, Adam) run in its documented order and
+    learning-rate schedule -- to rounding, since the loss sums and weight
+    gradients are accumulated with floating-point atomics -- and not those
+    of another order."""
+    learned, sld = env
+    n = 16
+    data = [learned.make_sample(s, n, m=12) for s in range(5)]
+    Ks, Vs, Ds = [d["K"] for d in data], [d["V"] for d in data], [d["D"] for d in data]
+    p0 = learned.init_params(3)
+    epochs, lr, decay, every, seed = 4, 3e-3, 0.5, 2, 11
+    a = sld.Net((n, n, n))
+    a.set_params(p0)
+    hist = a.train(Ks, Vs, Ds, epochs=epochs, lr=lr, lr_decay=decay, decay_every=every, seed=seed)
+    def loop(order_of):
+        b = sld.Net((n, n, n))
+        b.set_params(p0)
+        step = 0
+        means = []
+        for ep in range(epochs):
+            lr_ep = np.float32(lr) * np.float32(decay) ** np.float32(ep // every)
+            losses = []
+            for i in order_of(ep):
+                b.forward(Ks[i], keep=True)
+                losses.append(b.loss_backward(Vs[i], Ds[i]))
+                step += 1
+                b.adam(float(lr_ep), step)
+            means.append(np.mean(losses))
+        p = b.get_params()
+        b.close()
+        return np.array(means), p
+
+    means, pb = loop(lambda ep: _splitmix_order(len(data), seed + ep))
+    _, pw = loop(lambda ep: list(range(len(data)))[::-1])  # another order
+    pa = a.get_params()
+    np.testing.assert_allclose(hist, means, rtol=1e-3)
+    d_same, d_other = np.linalg.norm(pa - pb), np.linalg.norm(pa - pw)
+    print(f"parameters: documented loop {d_same:.2e} apart, another order {d_other:.2e} apart")
+    assert d_same <= 1e-3 * np.linalg.norm(pa) and d_same <= 0.1 * d_other
+    assert hist[-1] < hist[0]
+    with pytest.raises(sld.SldError):
+        a.train(Ks, Vs, Ds, epochs=0)
+    a.close()
+
+
+def test_learned_infer_equals_forward_and_build(env):
+    """sld_learned_infer (the network on the system's own K, appended to its
+    labels) builds the same deflation as sld_net_forward followed by
+    sld_build_deflation with those columns."""
+    import torch
+    learned, sld = env
+    n = 32
+    P = learned.field(learned.EVAL_SEED0 + 3, n)
+    net = sld.Net((n, n, n))
+    net.set_params(learned.init_params(5))
+    s1 = learned.build_system(P)
+    Y1 = torch.empty((P.n, 8), dtype=torch.float32, device="cuda")
+    net.infer(s1, out=Y1)
+    Y2 = net.forward(torch.from_numpy(P.K.reshape(-1)).cuda())
+    assert np.array_equal(Y1.cpu().numpy(), Y2)
+    s2 = learned.build_system(P)
+    s2.build_deflation(P.d, Zextra=Y2)
+    assert s1.deflation_info() == s2.deflation_info()
+    # E is assembled with FP64 atomics: two builds agree to rounding
+    E1, _ = s1.get_coarse()
+    E2, _ = s2.get_coarse()
+    assert np.max(np.abs(E1 - E2)) <= 1e-13 * np.max(np.abs(E1))
+    x1, i1 = s1.solve(precision=sld.FP64)
+    x2, i2 = s2.solve(precision=sld.FP64)
+    assert abs(i1.iterations - i2.iterations) <= 1
+    assert np.linalg.norm(x1 - x2) <= 1e-9 * np.linalg.norm(x2)
+    other = sld.Net((n, n, n // 2))
+    with pytest.raises(sld.SldError):
+        other.infer(s1)
+    other.close()
+    for s in (s1, s2):
+        s.close()
+    net.close()
