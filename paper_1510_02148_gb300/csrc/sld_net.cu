@@ -1,13 +1,15 @@
 // sld_net.cu -- the deflation-vector network: 3x3x3 convolutions as implicit
-// GEMMs on BF16 tensor cores (mma.sync m16n8k16, FP32 accumulation), their
-// data and weight gradients, pooling/upsampling, the subspace loss and Adam.
+// GEMMs on BF16 tensor cores (FP32 accumulation), their data and weight
+// gradients, pooling/upsampling, the subspace loss and Adam.
 //
 // Activations are channels-last BF16 [cell][C]; gradients of activations are
 // FP32.  A forward convolution is, per 3x3x3 tap, a GEMM of the shifted input
-// (cells x Cin) with the tap's weights (Cin x Cout): one warp owns 16
-// consecutive cells and all Cout columns.  The data gradient is the same
-// kernel on the flipped, transposed weights; the weight gradient is a GEMM
-// over cells (Cout x cells times cells x Cin per tap).
+// (cells x Cin) with the tap's weights (Cin x Cout), accumulated over the 27
+// taps: on the 5th-generation tensor cores (tcgen05.mma, accumulator in
+// tensor memory), one CTA per 128 cells and all Cout columns.  The data
+// gradient is the same kernel on the flipped, transposed weights; the weight
+// gradient is a GEMM over cells (Cout x cells times cells x Cin per tap),
+// also on tcgen05.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -17,6 +19,7 @@
 #include <vector>
 
 #include "../../include/sld_net.h"
+#include "sld_device.cuh"
 #include "sld_internal.h"
 
 namespace {
@@ -43,152 +46,338 @@ struct Dims {
 };
 Dims dims(int nx, int ny, int nz) { return Dims{nx, ny, nz, (int64_t)nx * ny, (int64_t)nx * ny * nz}; }
 
-__device__ __forceinline__ unsigned ld_b32(const bf16* p) { return *reinterpret_cast<const unsigned*>(p); }
 __device__ __forceinline__ unsigned pack2(bf16 lo, bf16 hi) {
   return (unsigned)__bfloat16_as_ushort(lo) | ((unsigned)__bfloat16_as_ushort(hi) << 16);
 }
 
-__device__ __forceinline__ void mma_bf16(float (&c)[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3,
-                                         unsigned b0, unsigned b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
 
-// Linear index of the neighbour of cell r at tap offset, or -1.
-__device__ __forceinline__ int64_t nbr(const Dims& d, int64_t r, int dz, int dy, int dx) {
-  if (r < 0 || r >= d.n) return -1;
-  const int x = (int)(r % d.nx), y = (int)((r / d.nx) % d.ny), z = (int)(r / d.nxy);
-  const int xx = x + dx, yy = y + dy, zz = z + dz;
-  if (xx < 0 || xx >= d.nx || yy < 0 || yy >= d.ny || zz < 0 || zz >= d.nz) return -1;
-  return r + (int64_t)dz * d.nxy + (int64_t)dy * d.nx + dx;
-}
 
 // ---------------------------------------------------------------------------
 // Convolution: Y[r][co] = epi(sum_t sum_ci W[t][co][ci] X[r + off_t][ci])
-// with epi = + bias, + skip, relu as requested.  Cin a multiple of 8, Cout =
-// 8 * NT.  One warp: cells m0 .. m0+15 (A rows), all Cout (NT n8 tiles).
+// with epi = + bias, + skip, relu as requested.
+// The same convolution on the 5th-generation tensor cores (tcgen05): one CTA
+// of 128 threads owns 128 consecutive cells (the M = 128 rows of the GEMM)
+// and all NP output channels (N, Cout padded to a multiple of 16); the FP32
+// accumulator lives in tensor memory (TMEM, NP of its columns).  For each of
+// the 27 taps every thread gathers its cell's neighbour row (Cin BF16,
+// zero-padded to CINP) into shared memory and the CTA loads the tap's
+// weights; one thread issues the CINP/16 MMAs (K = 16 each) of the tap and
+// commits them to the stage's mbarrier.  Two stages: the gather of tap t+1
+// overlaps the MMAs of tap t.  Operands use the canonical K-major layout
+// without swizzle: 8 x 8 BF16 core matrices of 128 contiguous bytes, the
+// ones adjacent in K 128 B apart (LBO), the 8-row groups CINP / 8 * 128 B
+// apart (SBO).  Every wait is bounded; a wait that runs out sets *err,
+// lets the MMAs in flight finish (bounded), frees the TMEM and leaves.
 // ---------------------------------------------------------------------------
-template <int NT>
-__global__ void __launch_bounds__(128) k_conv(Dims d, int Cin, const bf16* __restrict__ X,
-                                              const bf16* __restrict__ W, const float* __restrict__ bias,
-                                              const bf16* __restrict__ skip, int relu, bf16* __restrict__ Y16,
-                                              float* __restrict__ Y32) {
-  constexpr int Cout = 8 * NT;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t m0 = ((int64_t)blockIdx.x * 4 + warp) * 16;
-  if (m0 >= d.n) return;
-  const int g = lane >> 2, t = lane & 3;
-  const int64_t r0 = m0 + g, r1 = m0 + g + 8;
-  float acc[NT][4];
-#pragma unroll
-  for (int j = 0; j < NT; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-  for (int tap = 0; tap < 27; ++tap) {
-    const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-    const int64_t q0 = nbr(d, r0, dz, dy, dx), q1 = nbr(d, r1, dz, dy, dx);
-    const bf16* x0 = X + (q0 < 0 ? 0 : q0) * Cin;
-    const bf16* x1 = X + (q1 < 0 ? 0 : q1) * Cin;
-    const bf16* wt = W + (int64_t)tap * Cout * Cin;
-    for (int c0 = 0; c0 < Cin; c0 += 16) {
-      const bool hi = c0 + 8 < Cin;
-      const unsigned a0 = q0 >= 0 ? ld_b32(x0 + c0 + 2 * t) : 0u;
-      const unsigned a1 = q1 >= 0 ? ld_b32(x1 + c0 + 2 * t) : 0u;
-      const unsigned a2 = (q0 >= 0 && hi) ? ld_b32(x0 + c0 + 8 + 2 * t) : 0u;
-      const unsigned a3 = (q1 >= 0 && hi) ? ld_b32(x1 + c0 + 8 + 2 * t) : 0u;
-#pragma unroll
-      for (int j = 0; j < NT; ++j) {
-        const bf16* wr = wt + (int64_t)(j * 8 + g) * Cin + c0 + 2 * t;
-        const unsigned b0 = ld_b32(wr);
-        const unsigned b1 = hi ? ld_b32(wr + 8) : 0u;
-        mma_bf16(acc[j], a0, a1, a2, a3, b0, b1);
-      }
-    }
-  }
-#pragma unroll
-  for (int j = 0; j < NT; ++j) {
-    const int co = j * 8 + 2 * t;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int64_t r = h ? r1 : r0;
-      if (r >= d.n) continue;
-      float v0 = acc[j][2 * h], v1 = acc[j][2 * h + 1];
-      if (bias) {
-        v0 += bias[co];
-        v1 += bias[co + 1];
-      }
-      if (skip) {
-        v0 += __bfloat162float(skip[r * Cout + co]);
-        v1 += __bfloat162float(skip[r * Cout + co + 1]);
-      }
-      if (relu) {
-        v0 = fmaxf(v0, 0.f);
-        v1 = fmaxf(v1, 0.f);
-      }
-      if (Y16) *reinterpret_cast<unsigned*>(Y16 + r * Cout + co) = pack2(__float2bfloat16(v0), __float2bfloat16(v1));
-      if (Y32) *reinterpret_cast<float2*>(Y32 + r * Cout + co) = make_float2(v0, v1);
-    }
-  }
+__device__ __forceinline__ uint64_t umma_desc(const void* p, unsigned lbo, unsigned sbo) {
+  const uint64_t a = sld::smem_u32(p);
+  return ((a >> 4) & 0x3FFFull) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);  // version 1, no swizzle
 }
 
-// Weight gradient: dW[t][co][ci] += sum over cells r of G[r][co] X[r + off_t][ci].
-// One warp: one tap, 16 output channels (rows co0 .. co0+15, zero past
-// Cout), all Cin (NT n8 tiles), cells [r_beg, r_end) in k-steps of 16.
-template <int NT>
-__global__ void __launch_bounds__(128) k_wgrad(Dims d, int Cout, const bf16* __restrict__ G,
-                                               const bf16* __restrict__ X, float* __restrict__ dW, int64_t chunk) {
-  constexpr int Cin = 8 * NT;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int g = lane >> 2, t = lane & 3;
+// kind::f16 instruction descriptor: D FP32, A and B BF16, both K-major.
+__host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tmem_alloc(unsigned* dst, unsigned ncols) {  // one whole warp
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sld::smem_u32(dst)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(unsigned taddr, unsigned ncols) {  // one whole warp
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+__device__ __forceinline__ void umma_bf16(unsigned d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          unsigned accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   sld::smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 16 consecutive FP32 columns of the warp's 32 TMEM lanes (one lane per thread).
+__device__ __forceinline__ void tmem_ld16(unsigned taddr, float (&v)[16]) {
+  unsigned r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+template <int CINP, int NP>
+struct ConvTc {
+  static constexpr int KC = CINP / 8;                           // core matrices along K
+  static constexpr unsigned A_BYTES = 128u * CINP * 2u;         // one stage of A (128 rows)
+  static constexpr unsigned B_BYTES = (unsigned)NP * CINP * 2u;  // one stage of B (NP rows)
+  static constexpr unsigned SMEM = 2u * (A_BYTES + B_BYTES);
+  static constexpr unsigned NCOLS = NP <= 32 ? 32u : 64u;        // TMEM columns (a power of 2, >= 32)
+  static_assert(CINP % 16 == 0 && NP % 16 == 0 && NP <= 64 && CINP <= 64, "tile sizes");
+};
+
+template <int CINP, int NP>
+__global__ void __launch_bounds__(128) k_conv_tc(Dims d, int Cin, int Cout, const bf16* __restrict__ X,
+                                                 const bf16* __restrict__ W, const float* __restrict__ bias,
+                                                 const bf16* __restrict__ skip, int relu, bf16* __restrict__ Y16,
+                                                 float* __restrict__ Y32, int* __restrict__ err) {
+  using C = ConvTc<CINP, NP>;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ uint64_t mbar[2];
+  __shared__ unsigned tmem_base;
+  __shared__ int s_fail;
+  unsigned char* const As[2] = {smem, smem + C::A_BYTES};
+  unsigned char* const Bs[2] = {smem + 2 * C::A_BYTES, smem + 2 * C::A_BYTES + C::B_BYTES};
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const unsigned long long timeout = 2000000000ull;  // 2 s per wait
+  if (warp == 0) tmem_alloc(&tmem_base, C::NCOLS);
+  if (tid == 0) {
+    sld::mbar_init(&mbar[0], 1);
+    sld::mbar_init(&mbar[1], 1);
+    sld::fence_mbar_init();
+    s_fail = 0;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const unsigned tm = tmem_base;
+  const int64_t r = (int64_t)blockIdx.x * 128 + tid;  // this thread's cell (row)
+  int x = 0, y = 0, z = 0;
+  if (r < d.n) {
+    x = (int)(r % d.nx);
+    y = (int)((r / d.nx) % d.ny);
+    z = (int)(r / d.nxy);
+  }
+  constexpr uint32_t idesc = umma_idesc_bf16(128, NP);
+  int issued = 0;  // taps whose MMAs were issued (thread 0's view, shared below)
+  for (int tap = 0; tap < 27; ++tap) {
+    const int s = tap & 1;
+    if (tap >= 2 && !sld::mbar_wait_bounded(&mbar[s], (unsigned)(((tap - 2) >> 1) & 1), timeout)) s_fail = 1;
+    __syncthreads();  // stage s is free (or a wait failed: every thread sees s_fail)
+    if (s_fail) break;
+    // gather: this thread's neighbour row for the tap, Cin BF16 zero-padded to CINP
+    const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+    const int xx = x + dx, yy = y + dy, zz = z + dz;
+    const bool in = r < d.n && xx >= 0 && xx < d.nx && yy >= 0 && yy < d.ny && zz >= 0 && zz < d.nz;
+    const bf16* src = X + (in ? (r + (int64_t)dz * d.nxy + (int64_t)dy * d.nx + dx) * Cin : 0);
+    unsigned char* arow = As[s] + (tid >> 3) * (C::KC * 128) + (tid & 7) * 16;
+#pragma unroll
+    for (int j = 0; j < C::KC; ++j) {
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (in && 8 * j < Cin) v = *reinterpret_cast<const uint4*>(src + 8 * j);
+      *reinterpret_cast<uint4*>(arow + j * 128) = v;
+    }
+    // the tap's weights W[tap][co][ci] (K-major rows), zero-padded to NP x CINP
+    for (int i = tid; i < NP * C::KC; i += 128) {
+      const int co = i / C::KC, j = i % C::KC;
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (co < Cout && 8 * j < Cin) v = *reinterpret_cast<const uint4*>(W + ((int64_t)tap * Cout + co) * Cin + 8 * j);
+      *reinterpret_cast<uint4*>(Bs[s] + (co >> 3) * (C::KC * 128) + j * 128 + (co & 7) * 16) = v;
+    }
+    sld::fence_proxy_async_smem();  // the generic stores above, before the tensor core reads them
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+#pragma unroll
+      for (int kk = 0; kk < CINP / 16; ++kk) {
+        const uint64_t ad = umma_desc(As[s] + kk * 256, 128, C::KC * 128);
+        const uint64_t bd = umma_desc(Bs[s] + kk * 256, 128, C::KC * 128);
+        umma_bf16(tm, ad, bd, idesc, (tap > 0 || kk > 0) ? 1u : 0u);
+      }
+      umma_commit(&mbar[s]);
+    }
+    issued = tap + 1;
+  }
+  // wait for the last commit of each stage used (it covers every earlier MMA
+  // of the issuing thread): the last tap of stage s is the largest t < issued
+  // with t & 1 == s, its commit is use number t >> 1 of that stage
+  bool ok = !s_fail;
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const int t = (issued - 1) - (((issued - 1) & 1) ^ s);
+    if (t >= 0 && !sld::mbar_wait_bounded(&mbar[s], (unsigned)((t >> 1) & 1), timeout)) ok = false;
+  }
+  if (!ok && tid == 0) atomicExch(err, 1);
+  tc_fence_after();
+  if (ok) {
+#pragma unroll
+    for (int c0 = 0; c0 < NP; c0 += 16) {
+      float v[16];
+      tmem_ld16(tm + ((unsigned)(warp * 32) << 16) + (unsigned)c0, v);
+      if (r < d.n) {
+#pragma unroll
+        for (int j = 0; j < 16; j += 2) {
+          const int co = c0 + j;
+          if (co >= Cout) break;
+          float v0 = v[j], v1 = v[j + 1];
+          if (bias) {
+            v0 += bias[co];
+            v1 += bias[co + 1];
+          }
+          if (skip) {
+            v0 += __bfloat162float(skip[r * Cout + co]);
+            v1 += __bfloat162float(skip[r * Cout + co + 1]);
+          }
+          if (relu) {
+            v0 = fmaxf(v0, 0.f);
+            v1 = fmaxf(v1, 0.f);
+          }
+          if (Y16) *reinterpret_cast<unsigned*>(Y16 + r * Cout + co) = pack2(__float2bfloat16(v0), __float2bfloat16(v1));
+          if (Y32) *reinterpret_cast<float2*>(Y32 + r * Cout + co) = make_float2(v0, v1);
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tm, C::NCOLS);
+}
+
+// ---------------------------------------------------------------------------
+// Weight gradient on the tensor cores: for one tap and one chunk of cells,
+// dW[tap][co][ci] += sum_r G[r][co] X[r + off][ci], a GEMM with M = Cout
+// (padded to 128: the accumulator's TMEM lane is the output channel), N =
+// CINP = Cin and K = the chunk's cells, 64 per stage (four K = 16 MMAs).
+// Staging transposes both operands into K-major core matrices (8 rows x 8
+// cells): threads 0..63 scatter the G row of one cell, threads 64..127 the
+// shifted X row.  Rows co >= Cout of A stay zero.  Two stages, bounded waits
+// and the error path as in k_conv_tc; the chunk's result is added to dW with
+// FP32 atomics (chunks run in any order).
+// ---------------------------------------------------------------------------
+template <int CINP>
+struct WgradTc {
+  static constexpr int KB = 64;                                  // cells per stage
+  static constexpr unsigned A_BYTES = 128u * KB * 2u;            // 128 rows (co) x KB cells
+  static constexpr unsigned B_BYTES = (unsigned)CINP * KB * 2u;  // CINP rows (ci) x KB cells
+  static constexpr unsigned SMEM = 2u * (A_BYTES + B_BYTES);
+  static constexpr unsigned NCOLS = CINP <= 32 ? 32u : 64u;
+  static constexpr unsigned SBO = KB / 8 * 128;                  // next 8-row group
+};
+
+template <int CINP>
+__global__ void __launch_bounds__(128) k_wgrad_tc(Dims d, int Cout, const bf16* __restrict__ G,
+                                                  const bf16* __restrict__ X, float* __restrict__ dW, int64_t chunk,
+                                                  int* __restrict__ err) {
+  using C = WgradTc<CINP>;
+  constexpr int Cin = CINP;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ uint64_t mbar[2];
+  __shared__ unsigned tmem_base;
+  __shared__ int s_fail;
+  unsigned char* const As[2] = {smem, smem + C::A_BYTES};
+  unsigned char* const Bs[2] = {smem + 2 * C::A_BYTES, smem + 2 * C::A_BYTES + C::B_BYTES};
+  const int tid = threadIdx.x, warp = tid >> 5;
   const int tap = blockIdx.y;
-  const int co0 = (blockIdx.z * 4 + warp) * 16;
-  if (co0 >= Cout) return;
   const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+  const unsigned long long timeout = 2000000000ull;
+  if (warp == 0) tmem_alloc(&tmem_base, C::NCOLS);
+  // rows co >= Cout of both A stages stay zero
+  for (unsigned i = tid * 16; i < 2 * C::A_BYTES; i += 128 * 16) *reinterpret_cast<uint4*>(smem + i) = make_uint4(0u, 0u, 0u, 0u);
+  if (tid == 0) {
+    sld::mbar_init(&mbar[0], 1);
+    sld::mbar_init(&mbar[1], 1);
+    sld::fence_mbar_init();
+    s_fail = 0;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const unsigned tm = tmem_base;
   const int64_t rb = (int64_t)blockIdx.x * chunk;
   const int64_t re = min(rb + chunk, d.n);
-  const int coA = co0 + g, coB = co0 + g + 8;
-  const bool okA = coA < Cout, okB = coB < Cout;
-  const bf16 z = __float2bfloat16(0.f);
-  float acc[NT][4];
+  const int nst = (int)((re - rb + C::KB - 1) / C::KB);
+  constexpr uint32_t idesc = umma_idesc_bf16(128, CINP);
+  int issued = 0;
+  for (int st = 0; st < nst; ++st) {
+    const int s = st & 1;
+    if (st >= 2 && !sld::mbar_wait_bounded(&mbar[s], (unsigned)(((st - 2) >> 1) & 1), timeout)) s_fail = 1;
+    __syncthreads();
+    if (s_fail) break;
+    const int c = tid & 63;  // the cell of this thread within the stage
+    const int64_t r = rb + (int64_t)st * C::KB + c;
+    const unsigned cell_off = (unsigned)(c >> 3) * 128u + (unsigned)(c & 7) * 2u;
+    if (tid < 64) {  // A[co][c] = G[r][co]
+      for (int co0 = 0; co0 < Cout; co0 += 8) {
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (r < re) v = *reinterpret_cast<const uint4*>(G + r * Cout + co0);
+        const bf16* e = reinterpret_cast<const bf16*>(&v);
 #pragma unroll
-  for (int j = 0; j < NT; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-  for (int64_t p0 = rb; p0 < re; p0 += 16) {
-    // the four cells this thread touches in this k-step
-    const int64_t pc[4] = {p0 + 2 * t, p0 + 2 * t + 1, p0 + 2 * t + 8, p0 + 2 * t + 9};
-    bf16 gA[4], gB[4];
-    int64_t q[4];
+        for (int k = 0; k < 8; ++k)
+          *reinterpret_cast<bf16*>(As[s] + (unsigned)(co0 >> 3) * C::SBO + (unsigned)k * 16u + cell_off) = e[k];
+      }
+    } else {  // B[ci][c] = X[r + off][ci]
+      int64_t q = -1;
+      if (r < re) {
+        const int x = (int)(r % d.nx), y = (int)((r / d.nx) % d.ny), z = (int)(r / d.nxy);
+        const int xx = x + dx, yy = y + dy, zz = z + dz;
+        if (xx >= 0 && xx < d.nx && yy >= 0 && yy < d.ny && zz >= 0 && zz < d.nz)
+          q = r + (int64_t)dz * d.nxy + (int64_t)dy * d.nx + dx;
+      }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const bool in = pc[u] < re;
-      gA[u] = (in && okA) ? G[pc[u] * Cout + coA] : z;
-      gB[u] = (in && okB) ? G[pc[u] * Cout + coB] : z;
-      q[u] = in ? nbr(d, pc[u], dz, dy, dx) : -1;
+      for (int ci0 = 0; ci0 < Cin; ci0 += 8) {
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (q >= 0) v = *reinterpret_cast<const uint4*>(X + q * Cin + ci0);
+        const bf16* e = reinterpret_cast<const bf16*>(&v);
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          *reinterpret_cast<bf16*>(Bs[s] + (unsigned)(ci0 >> 3) * C::SBO + (unsigned)k * 16u + cell_off) = e[k];
+      }
     }
-    const unsigned a0 = pack2(gA[0], gA[1]), a1 = pack2(gB[0], gB[1]);
-    const unsigned a2 = pack2(gA[2], gA[3]), a3 = pack2(gB[2], gB[3]);
+    sld::fence_proxy_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
 #pragma unroll
-    for (int j = 0; j < NT; ++j) {
-      const int ci = j * 8 + g;
-      bf16 xv[4];
+      for (int kk = 0; kk < C::KB / 16; ++kk) {
+        const uint64_t ad = umma_desc(As[s] + kk * 256, 128, C::SBO);
+        const uint64_t bd = umma_desc(Bs[s] + kk * 256, 128, C::SBO);
+        umma_bf16(tm, ad, bd, idesc, (st > 0 || kk > 0) ? 1u : 0u);
+      }
+      umma_commit(&mbar[s]);
+    }
+    issued = st + 1;
+  }
+  bool ok = !s_fail && issued > 0;
 #pragma unroll
-      for (int u = 0; u < 4; ++u) xv[u] = q[u] >= 0 ? X[q[u] * Cin + ci] : z;
-      mma_bf16(acc[j], a0, a1, a2, a3, pack2(xv[0], xv[1]), pack2(xv[2], xv[3]));
+  for (int s = 0; s < 2; ++s) {
+    const int t = (issued - 1) - (((issued - 1) & 1) ^ s);
+    if (t >= 0 && !sld::mbar_wait_bounded(&mbar[s], (unsigned)((t >> 1) & 1), timeout)) ok = false;
+  }
+  if (!ok && issued > 0 && tid == 0) atomicExch(err, 1);
+  tc_fence_after();
+  if (ok) {
+    const int co = tid;  // TMEM lane = output channel
+    float* base = dW + ((int64_t)tap * Cout + co) * Cin;
+#pragma unroll
+    for (int c0 = 0; c0 < CINP; c0 += 16) {
+      float v[16];
+      tmem_ld16(tm + ((unsigned)(warp * 32) << 16) + (unsigned)c0, v);
+      if (co < Cout) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) atomicAdd(base + c0 + j, v[j]);
+      }
     }
   }
-#pragma unroll
-  for (int j = 0; j < NT; ++j) {
-    const int ci = j * 8 + 2 * t;
-    float* base = dW + (int64_t)tap * Cout * Cin;
-    if (okA) {
-      atomicAdd(base + (int64_t)coA * Cin + ci, acc[j][0]);
-      atomicAdd(base + (int64_t)coA * Cin + ci + 1, acc[j][1]);
-    }
-    if (okB) {
-      atomicAdd(base + (int64_t)coB * Cin + ci, acc[j][2]);
-      atomicAdd(base + (int64_t)coB * Cin + ci + 1, acc[j][3]);
-    }
-  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tm, C::NCOLS);
 }
 
 // Wt[26 - t][ci][co] = W[t][co][ci]: the weights of the data-gradient convolution.
@@ -434,6 +623,7 @@ struct sld_net_s {
   bf16* dz = nullptr;
   float* Vst = nullptr;   // staged targets
   double* Dst = nullptr;  // staged weights
+  int* err = nullptr;     // set by a tensor-core kernel whose bounded wait ran out
   std::vector<void*> allocs;
 };
 
@@ -446,6 +636,20 @@ sld_status nfail(sld_status st, const std::string& m) {
 sld_status ncuda(cudaError_t e, const char* what) {
   return nfail(e == cudaErrorMemoryAllocation ? SLD_ERR_OOM : SLD_ERR_CUDA,
                std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// After a synchronised call: a tensor-core kernel whose bounded wait ran out
+// left *err set (and its results unwritten); report it and clear the flag.
+sld_status nchecked(sld_net net, cudaError_t e, const char* what) {
+  if (e != cudaSuccess) return ncuda(e, what);
+  int h = 0;
+  e = cudaMemcpy(&h, net->err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return ncuda(e, what);
+  if (h) {
+    cudaMemset(net->err, 0, sizeof(int));
+    return nfail(SLD_ERR_TIMEOUT, std::string(what) + ": a tensor-core wait timed out");
+  }
+  return SLD_OK;
 }
 bool on_dev(const void* p) {
   cudaPointerAttributes at;
@@ -467,25 +671,30 @@ cudaError_t nalloc(sld_net net, T** p, int64_t count) {
   return e;
 }
 
+// A convolution on the tensor cores: k_conv_tc with Cin and Cout padded to
+// multiples of 16 (the forward and data-gradient channel pairs of the net).
 cudaError_t conv(sld_net net, int level, int l, const bf16* X, const bf16* W, const float* bias, const bf16* skip,
                  int relu, bf16* Y16, float* Y32, int Cin, int Cout) {
   const Dims& d = net->d[level];
-  const unsigned grid = blocks(d.n, 64);
-  switch (Cout / 8) {
-#define CONV_CASE(NT)                                                                                         \
-  case NT:                                                                                                    \
-    k_conv<NT><<<grid, 128, 0, net->stream>>>(d, Cin, X, W, bias, skip, relu, Y16, Y32);                      \
-    break;
-    CONV_CASE(1)
-    CONV_CASE(2)
-    CONV_CASE(4)
-    CONV_CASE(6)
-    CONV_CASE(8)
-#undef CONV_CASE
-    default:
-      return cudaErrorInvalidValue;
+  const unsigned grid = blocks(d.n, 128);
+  const int cinp = (Cin + 15) / 16 * 16, np = (Cout + 15) / 16 * 16;
+  bool done = false;
+#define CONV_TC(CI, NN)                                                                                        \
+  if (!done && cinp == CI && np == NN) {                                                                       \
+    k_conv_tc<CI, NN><<<grid, 128, ConvTc<CI, NN>::SMEM, net->stream>>>(d, Cin, Cout, X, W, bias, skip, relu,  \
+                                                                        Y16, Y32, net->err);                   \
+    done = true;                                                                                               \
   }
+  CONV_TC(16, 16)
+  CONV_TC(16, 32)
+  CONV_TC(32, 16)
+  CONV_TC(32, 48)
+  CONV_TC(48, 32)
+  CONV_TC(48, 64)
+  CONV_TC(64, 48)
+#undef CONV_TC
   (void)l;
+  if (!done) return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 
@@ -493,17 +702,20 @@ cudaError_t wgrad(sld_net net, int level, int l, const bf16* Gz, const bf16* X) 
   const Dims& d = net->d[level];
   const int Cin = kCin[l], Cout = kCout[l];
   const int64_t chunk = 4096;
-  dim3 grid((unsigned)((d.n + chunk - 1) / chunk), 27, (unsigned)((Cout + 63) / 64));
+  dim3 grid((unsigned)((d.n + chunk - 1) / chunk), 27, 1);
   float* dW = net->G + w_off(l);
-  switch (Cin / 8) {
-#define WG_CASE(NT)                                                                     \
-  case NT:                                                                              \
-    k_wgrad<NT><<<grid, 128, 0, net->stream>>>(d, Cout, Gz, X, dW, chunk);              \
-    break;
-    WG_CASE(2)
-    WG_CASE(4)
-    WG_CASE(6)
-    WG_CASE(8)
+  switch (Cin) {
+#define WG_CASE(CI)                                                                                        \
+  case CI: {                                                                                               \
+    auto kern = k_wgrad_tc<CI>;                                                                            \
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)WgradTc<CI>::SMEM);       \
+    kern<<<grid, 128, WgradTc<CI>::SMEM, net->stream>>>(d, Cout, Gz, X, dW, chunk, net->err);              \
+    break;                                                                                                 \
+  }
+    WG_CASE(16)
+    WG_CASE(32)
+    WG_CASE(48)
+    WG_CASE(64)
 #undef WG_CASE
     default:
       return cudaErrorInvalidValue;
@@ -637,6 +849,7 @@ sld_status sld_net_create(int nx, int ny, int nz, void* stream, sld_net* out) {
   A(nalloc(net, &net->d1, n1 * 32));
   A(nalloc(net, &net->u0, n0 * 32));
   A(nalloc(net, &net->d0, n0 * 16));
+  A(nalloc(net, &net->err, 1));
   A(nalloc(net, &net->out, n0 * kOutC));
   A(nalloc(net, &net->gout, n0 * kOutC));
   A(nalloc(net, &net->g0a, n0 * 16));
@@ -657,6 +870,7 @@ sld_status sld_net_create(int nx, int ny, int nz, void* stream, sld_net* out) {
     cudaMemsetAsync(net->M, 0, sizeof(float) * net->np, net->stream);
     cudaMemsetAsync(net->V, 0, sizeof(float) * net->np, net->stream);
     cudaMemsetAsync(net->G, 0, sizeof(float) * net->np, net->stream);
+    cudaMemsetAsync(net->err, 0, sizeof(int), net->stream);
     e = cudaStreamSynchronize(net->stream);
   }
   if (e != cudaSuccess) {
@@ -701,7 +915,7 @@ sld_status sld_net_forward(sld_net net, const double* K, float* out) {
   if (e == cudaSuccess && out)
     e = cudaMemcpyAsync(out, net->out, sizeof(float) * d.n * kOutC, cudaMemcpyDefault, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  return e == cudaSuccess ? SLD_OK : ncuda(e, "network forward");
+  return nchecked(net, e, "network forward");
 }
 
 sld_status sld_net_backward(sld_net net, const float* dout) {
@@ -710,7 +924,7 @@ sld_status sld_net_backward(sld_net net, const float* dout) {
   cudaError_t e = cudaMemcpyAsync(net->gout, dout, sizeof(float) * d.n * kOutC, cudaMemcpyDefault, net->stream);
   if (e == cudaSuccess) e = backward(net);
   if (e == cudaSuccess) e = cudaStreamSynchronize(net->stream);
-  return e == cudaSuccess ? SLD_OK : ncuda(e, "network backward");
+  return nchecked(net, e, "network backward");
 }
 
 sld_status sld_net_loss_backward(sld_net net, const float* V, int m, const double* D, double* loss) {
@@ -782,7 +996,7 @@ sld_status sld_net_loss_backward(sld_net net, const float* V, int m, const doubl
   k_loss_grad<<<blocks(d.n, 256), 256, 0, s>>>(d.n, sm, net->out, Vd, Dd, net->gout);
   e = backward(net);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  return e == cudaSuccess ? SLD_OK : ncuda(e, "loss backward");
+  return nchecked(net, e, "loss backward");
 }
 
 sld_status sld_net_adam(sld_net net, float lr, float beta1, float beta2, float eps, int step) {
