@@ -566,7 +566,7 @@ void sld_destroy(sld_system s) {
   void* ptrs[] = {s->K, s->Tx, s->Ty, s->Tz, s->diag, s->invdiag, s->b, s->Tx32, s->Ty32, s->Tz32,
                   s->Tx16, s->Ty16, s->Tz16, s->invd16, s->E16, s->Einv16,
                   s->label, s->label16, s->E, s->Einv, s->ZL32, s->WL64, s->WL32, s->x, s->r64, s->bwork, s->z, s->p0, s->p1, s->xh,
-                  s->part, s->s_glob, s->y_glob, s->out, s->bar, s->status, s->gacc};
+                  s->part, s->s_glob, s->y_glob, s->out, s->bar, s->status, s->gacc, s->gm_ws};
   for (void* p : ptrs) dfree(p);
   if (s->ev0) cudaEventDestroy(s->ev0);
   if (s->ev1) cudaEventDestroy(s->ev1);
@@ -919,6 +919,21 @@ cudaError_t ensure_gacc(sld_system s, size_t doubles) {
   }
   cudaError_t e = cudaMalloc(&s->gacc, sizeof(double) * doubles);
   if (e == cudaSuccess) s->gacc_cap = doubles;
+  return e;
+}
+}  // namespace sld
+
+namespace sld {
+cudaError_t ensure_gmres_ws(sld_system s, size_t doubles) {
+  if (doubles <= s->gm_ws_cap && s->gm_ws) return cudaSuccess;
+  if (s->gm_ws) {
+    cudaStreamSynchronize(s->stream);
+    cudaFree(s->gm_ws);
+    s->gm_ws = nullptr;
+    s->gm_ws_cap = 0;
+  }
+  cudaError_t e = cudaMalloc(&s->gm_ws, sizeof(double) * doubles);
+  if (e == cudaSuccess) s->gm_ws_cap = doubles;
   return e;
 }
 }  // namespace sld

@@ -15,16 +15,21 @@
 //   k_gm_orth      w -= V h1
 //   k_gm_dots      h2 = V^T w
 //   k_gm_orth      raw = w - V h2, |raw|^2
+//   k_gm_givens    the Hessenberg column, the Givens rotations, the test
 // Classical Gram-Schmidt with one reorthogonalisation (two passes over the
 // basis, each fully parallel) stands in for the sequential modified
-// Gram-Schmidt; the Hessenberg column is h1 + h2 and h_{j+1,j} = |raw|.  One
-// device-to-host copy per step brings it to the host, which applies the
-// Givens rotations, tests the residual estimate and, at the end of a cycle,
-// solves the small triangular system.  Every sum is a per-CTA partial row
-// reduced in a fixed order.
+// Gram-Schmidt; the Hessenberg column is h1 + h2 and h_{j+1,j} = |raw|.  The
+// rotations and the residual test run on the device (k_gm_givens), so a
+// cycle's steps are launched without host round trips; once the test stops
+// the cycle, the kernels of the remaining steps return at once.  The host
+// reads the rotated Hessenberg matrix once per cycle and solves the small
+// triangular system.  Every sum is a per-CTA partial row reduced in a fixed
+// order.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -47,7 +52,9 @@ enum { GM_PRECOND = 0, GM_RESID = 1, GM_APPLY = 2, GM_COPY = 3, GM_BAPPLY = 4 };
 template <int MODE, bool WACC>
 __global__ void __launch_bounds__(kGT) k_gm_apply(SolveArgs a, const double* __restrict__ v,
                                                   const double* __restrict__ norm2, double* __restrict__ vout,
-                                                  double* __restrict__ w, double* __restrict__ part) {
+                                                  double* __restrict__ w, double* __restrict__ part,
+                                                  const int* __restrict__ stop = nullptr) {
+  if (stop && *stop) return;  // the device Givens step ended the cycle
   extern __shared__ double sacc[];
   const int d = a.d;
   const int warp = threadIdx.x >> 5;
@@ -116,7 +123,9 @@ __global__ void __launch_bounds__(kGT) k_gm_apply(SolveArgs a, const double* __r
 
 // out[k] = sum of column k of the partial rows (G CTAs), k < ncol; one warp
 // per column, the same order every time.
-__global__ void k_gm_colsum(const double* __restrict__ part, int pstride, int G, int ncol, double* __restrict__ out) {
+__global__ void k_gm_colsum(const double* __restrict__ part, int pstride, int G, int ncol, double* __restrict__ out,
+                            const int* __restrict__ stop = nullptr) {
+  if (stop && *stop) return;
   const int col = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   if (col >= ncol) return;
   const double* p = part + (int64_t)col * pstride;
@@ -127,7 +136,9 @@ __global__ void k_gm_colsum(const double* __restrict__ part, int pstride, int G,
 }
 
 // y = E^{-1} s, one warp per row.
-__global__ void k_gm_gemv(int d, const double* __restrict__ Einv, const double* __restrict__ s, double* __restrict__ y) {
+__global__ void k_gm_gemv(int d, const double* __restrict__ Einv, const double* __restrict__ s, double* __restrict__ y,
+                          const int* __restrict__ stop = nullptr) {
+  if (stop && *stop) return;
   const int row = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   if (row >= d) return;
   double t = 0.0;
@@ -137,7 +148,9 @@ __global__ void k_gm_gemv(int d, const double* __restrict__ Einv, const double* 
 }
 
 // w -= A Z y  ((A Z y)_i: the stencil applied to the cellwise y[label]).
-__global__ void __launch_bounds__(kGT) k_gm_defl(SolveArgs a, const double* __restrict__ y, double* __restrict__ w) {
+__global__ void __launch_bounds__(kGT) k_gm_defl(SolveArgs a, const double* __restrict__ y, double* __restrict__ w,
+                                                 const int* __restrict__ stop = nullptr) {
+  if (stop && *stop) return;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   CellWalk c;
   c.init(a, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, stride);
@@ -157,7 +170,8 @@ __global__ void __launch_bounds__(kGT) k_gm_defl(SolveArgs a, const double* __re
 // Partial rows of V_k . w for the kGDots basis vectors k0 = blockIdx.y * kGDots ..
 __global__ void __launch_bounds__(kGT) k_gm_dots(int64_t n, const double* __restrict__ V, int nv,
                                                  const double* __restrict__ w, double* __restrict__ part,
-                                                 int pstride) {
+                                                 int pstride, const int* __restrict__ stop = nullptr) {
+  if (stop && *stop) return;
   __shared__ double red[kGDots][kGT / 32];
   const int k0 = blockIdx.y * kGDots;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -187,7 +201,9 @@ __global__ void __launch_bounds__(kGT) k_gm_dots(int64_t n, const double* __rest
 // partial row of |out|^2 in that column.
 __global__ void __launch_bounds__(kGT) k_gm_orth(int64_t n, const double* __restrict__ V, int nv,
                                                  const double* __restrict__ h, const double* w, double* out,
-                                                 double* __restrict__ part, int pstride, int norm_col) {
+                                                 double* __restrict__ part, int pstride, int norm_col,
+                                                 const int* __restrict__ stop = nullptr) {
+  if (stop && *stop) return;
   __shared__ double hs[kGMaxBasis];
   __shared__ double red[kGT / 32];
   if (threadIdx.x < kGMaxBasis) hs[threadIdx.x] = (int)threadIdx.x < nv ? h[threadIdx.x] : 0.0;
@@ -209,6 +225,45 @@ __global__ void __launch_bounds__(kGT) k_gm_orth(int64_t n, const double* __rest
     for (int q = 0; q < kGT / 32; ++q) t += red[q];
     part[(int64_t)norm_col * pstride + blockIdx.x] = t;
   }
+}
+
+// The Givens step of GMRES on the device (one thread): Hessenberg column j =
+// h1 + h2 with h_{j+1,j} = |raw|, the earlier rotations applied, a new one
+// for row j+1, the rotated right-hand side g; the cycle stops (later kernels
+// of the cycle return at once) when |g_{j+1}| <= tol_abs, at a breakdown
+// (h_{j+1,j} = 0) or at the cycle's last step.
+struct GivensState {
+  double R[kGMaxBasis * kGMaxBasis];  // (m + 1) x m, row-major, pitch kGMaxBasis
+  double cs[kGMaxBasis], sn[kGMaxBasis], g[kGMaxBasis + 1];
+  double est;  // |g_k| after the last step
+  int k;       // steps done in this cycle
+  int stop;    // 1: the cycle is over
+};
+
+__global__ void k_gm_givens(const double* __restrict__ h1, const double* __restrict__ h2, const double* __restrict__ nn,
+                            GivensState* __restrict__ gs, int j, double tol_abs, int last) {
+  if (threadIdx.x != 0 || gs->stop) return;
+  double col[kGMaxBasis + 1];
+  for (int i = 0; i <= j; ++i) col[i] = h1[i] + h2[i];
+  const double hn = sqrt(*nn);
+  col[j + 1] = hn;
+  for (int i = 0; i < j; ++i) {
+    const double t = gs->cs[i] * col[i] + gs->sn[i] * col[i + 1];
+    col[i + 1] = -gs->sn[i] * col[i] + gs->cs[i] * col[i + 1];
+    col[i] = t;
+  }
+  const double rho = hypot(col[j], col[j + 1]);
+  const double c = rho == 0.0 ? 1.0 : col[j] / rho, sv = rho == 0.0 ? 0.0 : col[j + 1] / rho;
+  gs->cs[j] = c;
+  gs->sn[j] = sv;
+  col[j] = rho;
+  col[j + 1] = 0.0;
+  for (int i = 0; i <= j + 1; ++i) gs->R[i * kGMaxBasis + j] = col[i];
+  gs->g[j + 1] = -sv * gs->g[j];
+  gs->g[j] = c * gs->g[j];
+  gs->k = j + 1;
+  gs->est = fabs(gs->g[j + 1]);
+  if (gs->est <= tol_abs || hn == 0.0 || last) gs->stop = 1;
 }
 
 // x~ += M^{-1} sum_{k < nv} u[k] V_k
@@ -272,41 +327,42 @@ int run_gmres(sld_system s, const double* b, int m, int deflate, double tol, int
   a.sy.cta0 = 0;
   const int ps = a.pstride;
   double* part = a.part;
-  // work space: the basis (m + 1) n, w, raw, x~ (n each), small vectors
-  double* V = nullptr;
-  double* work = nullptr;
-  Scal* sc = nullptr;
+  // work space, kept by the handle between calls: the basis (m + 1) n, w,
+  // raw, x~ (n each), small vectors, the device scalars and Givens state
   const size_t small = (size_t)4 * (d + 1) + kGMaxBasis;
-  auto release = [&]() {
-    cudaFree(V);
-    cudaFree(work);
-    cudaFree(sc);
-  };
-  cudaError_t e = cudaMalloc(&V, sizeof(double) * (size_t)(m + 1) * n);
-  if (e == cudaSuccess) e = cudaMalloc(&work, sizeof(double) * ((size_t)3 * n + small));
-  if (e == cudaSuccess) e = cudaMalloc(&sc, sizeof(Scal));
+  const size_t scal_off = ((size_t)(m + 4) * n + small + 31) / 32 * 32;  // doubles, 256-byte aligned
+  const size_t gs_off = scal_off + (sizeof(Scal) + 255) / 256 * 32;
+  const size_t need = gs_off + (sizeof(GivensState) + 255) / 256 * 32;
+  cudaError_t e = ensure_gmres_ws(s, need);
   if (e != cudaSuccess) {
-    release();
     *msg = std::string("GMRES work space: ") + cudaGetErrorString(e);
     return SLD_ERR_OOM;
   }
+  auto release = [&]() {};
+  double* V = s->gm_ws;
+  double* work = V + (size_t)(m + 1) * n;
+  Scal* sc = reinterpret_cast<Scal*>(s->gm_ws + scal_off);
+  GivensState* gs = reinterpret_cast<GivensState*>(s->gm_ws + gs_off);
+  std::unique_ptr<GivensState> hgs_own(new GivensState());
+  GivensState* hgs = hgs_own.get();
   double *w = work, *raw = w + n, *xt = raw + n;
   double *sv = xt + n, *y = sv + (d + 1), *y0 = y + (d + 1), *y1 = y0 + (d + 1), *ud = y1 + (d + 1);
   const size_t smem = sizeof(double) * (size_t)(wacc ? kGT / 32 : 1) * (size_t)std::max(d, 1);
   // colsum / gemv: one warp per column (row), 8 warps per block
   auto cols = [&](int ncol) { return dim3((unsigned)((ncol + 7) / 8)); };
-  auto colsum = [&](int ncol, double* out) {
-    k_gm_colsum<<<cols(ncol), 256, 0, st>>>(part, ps, G, ncol, out);
+  auto colsum = [&](int ncol, double* out, const int* stp = nullptr) {
+    k_gm_colsum<<<cols(ncol), 256, 0, st>>>(part, ps, G, ncol, out, stp);
   };
   // s = Z^T (partials from the last k_gm_apply), y = E^{-1} s
   auto coarse = [&](double* yout) {
     colsum(d, sv);
     k_gm_gemv<<<cols(d), 256, 0, st>>>(d, a.Einv, sv, yout);
   };
-  auto apply = [&](int mode, const double* v, const double* nrm2, double* vout, double* wout) {
+  auto apply = [&](int mode, const double* v, const double* nrm2, double* vout, double* wout,
+                   const int* stp = nullptr) {
 #define GM_LAUNCH(MODE)                                                                              \
-  (wacc ? k_gm_apply<MODE, true><<<G, kGT, smem, st>>>(a, v, nrm2, vout, wout, part)                  \
-        : k_gm_apply<MODE, false><<<G, kGT, smem, st>>>(a, v, nrm2, vout, wout, part))
+  (wacc ? k_gm_apply<MODE, true><<<G, kGT, smem, st>>>(a, v, nrm2, vout, wout, part, stp)             \
+        : k_gm_apply<MODE, false><<<G, kGT, smem, st>>>(a, v, nrm2, vout, wout, part, stp))
     switch (mode) {
       case GM_PRECOND: GM_LAUNCH(GM_PRECOND); break;
       case GM_RESID: GM_LAUNCH(GM_RESID); break;
@@ -320,7 +376,7 @@ int run_gmres(sld_system s, const double* b, int m, int deflate, double tol, int
     colsum(nv, out);
   };
   // R: the Hessenberg matrix with the rotations applied (upper triangular part used)
-  std::vector<double> R((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), u(m);
+  std::vector<double> u(m);
   cudaEventRecord(s->ev0, st);
   // ||b||, and x* = Z y0 with y0 = E^{-1} Z^T b
   k_gm_orth<<<G, kGT, 0, st>>>(n, V, 0, sc->h1, b, raw, part, ps, 0);
@@ -364,57 +420,47 @@ int run_gmres(sld_system s, const double* b, int m, int deflate, double tol, int
     }
     if (its >= maxiter) break;
     ++cycles;
-    std::fill(g.begin(), g.end(), 0.0);
-    g[0] = beta;
-    int k = 0;
-    for (int j = 0; j < m; ++j) {
-      // v_j = raw / |raw|, w = P1 A M^{-1} v_j
-      apply(GM_PRECOND, raw, &sc->nn, V + (size_t)j * n, w);
+    // the cycle's steps run stream-ordered without host round trips: the
+    // Givens rotations and the residual test are a one-thread kernel per
+    // step, and once it stops the cycle the remaining kernels return at once
+    const int steps = std::min(m, maxiter - its);
+    hgs->k = 0;
+    hgs->stop = 0;
+    hgs->est = beta;
+    std::fill(hgs->g, hgs->g + kGMaxBasis + 1, 0.0);
+    hgs->g[0] = beta;
+    cudaMemcpyAsync(gs, hgs, sizeof(GivensState), cudaMemcpyHostToDevice, st);
+    const int* stp = &gs->stop;
+    for (int j = 0; j < steps; ++j) {
+      const int nv = j + 1;
+      // v_j = raw / |raw|, w = P1 A M^{-1} v_j, h1 = V^T w
+      apply(GM_PRECOND, raw, &sc->nn, V + (size_t)j * n, w, stp);
       if (d > 0) {
-        coarse(y);
-        k_gm_defl<<<G, kGT, 0, st>>>(a, y, w);
+        colsum(d, sv, stp);
+        k_gm_gemv<<<cols(d), 256, 0, st>>>(d, a.Einv, sv, y, stp);
+        k_gm_defl<<<G, kGT, 0, st>>>(a, y, w, stp);
       }
-      // classical Gram-Schmidt, twice
-      dots(j + 1, sc->h1);
-      k_gm_orth<<<G, kGT, 0, st>>>(n, V, j + 1, sc->h1, w, w, part, ps, -1);
-      dots(j + 1, sc->h2);
-      k_gm_orth<<<G, kGT, 0, st>>>(n, V, j + 1, sc->h2, w, raw, part, ps, 0);
-      colsum(1, &sc->nn);
-      if (!fetch()) break;
-      // Hessenberg column j, the earlier rotations, a new one for row j+1
-      std::vector<double> col(j + 2);
-      for (int i = 0; i <= j; ++i) col[i] = hs.h1[i] + hs.h2[i];
-      const double hn = std::sqrt(hs.nn);
-      col[j + 1] = hn;
-      for (int i = 0; i < j; ++i) {
-        const double t = cs[i] * col[i] + sn[i] * col[i + 1];
-        col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
-        col[i] = t;
-      }
-      const double rho = std::hypot(col[j], col[j + 1]);
-      if (rho == 0.0) {
-        cs[j] = 1.0;
-        sn[j] = 0.0;
-      } else {
-        cs[j] = col[j] / rho;
-        sn[j] = col[j + 1] / rho;
-      }
-      col[j] = rho;
-      col[j + 1] = 0.0;
-      for (int i = 0; i <= j + 1; ++i) R[(size_t)i * m + j] = col[i];
-      g[j + 1] = -sn[j] * g[j];
-      g[j] = cs[j] * g[j];
-      ++its;
-      k = j + 1;
-      est = std::fabs(g[j + 1]) / bnorm;
-      if (std::fabs(g[j + 1]) <= tol * bnorm || hn == 0.0 || its >= maxiter) break;
+      k_gm_dots<<<dim3(G, (nv + kGDots - 1) / kGDots), kGT, 0, st>>>(n, V, nv, w, part, ps, stp);
+      colsum(nv, sc->h1, stp);
+      // classical Gram-Schmidt, twice: w -= V h1, h2 = V^T w, raw = w - V h2 and |raw|^2
+      k_gm_orth<<<G, kGT, 0, st>>>(n, V, nv, sc->h1, w, w, part, ps, -1, stp);
+      k_gm_dots<<<dim3(G, (nv + kGDots - 1) / kGDots), kGT, 0, st>>>(n, V, nv, w, part, ps, stp);
+      colsum(nv, sc->h2, stp);
+      k_gm_orth<<<G, kGT, 0, st>>>(n, V, nv, sc->h2, w, raw, part, ps, 0, stp);
+      colsum(1, &sc->nn, stp);
+      k_gm_givens<<<1, 32, 0, st>>>(sc->h1, sc->h2, &sc->nn, gs, j, tol * bnorm, j + 1 == steps ? 1 : 0);
     }
-    if (e != cudaSuccess) break;
+    if ((e = cudaMemcpyAsync(hgs, gs, sizeof(GivensState), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+      break;
+    const int k = hgs->k;
+    its += k;
+    est = bnorm > 0 ? hgs->est / bnorm : 0.0;
     // R u = g (upper triangular, k x k), then x~ += M^{-1} V u
     for (int i = k - 1; i >= 0; --i) {
-      double t = g[i];
-      for (int q = i + 1; q < k; ++q) t -= R[(size_t)i * m + q] * u[q];
-      u[i] = R[(size_t)i * m + i] != 0.0 ? t / R[(size_t)i * m + i] : 0.0;
+      double t = hgs->g[i];
+      for (int q = i + 1; q < k; ++q) t -= hgs->R[i * kGMaxBasis + q] * u[q];
+      u[i] = hgs->R[i * kGMaxBasis + i] != 0.0 ? t / hgs->R[i * kGMaxBasis + i] : 0.0;
     }
     if (k > 0) {
       cudaMemcpyAsync(ud, u.data(), sizeof(double) * k, cudaMemcpyHostToDevice, st);

@@ -137,6 +137,8 @@ struct sld_system_s {
   int part_rows = 0;
   double* gacc = nullptr;  // global per-warp label-sum rows (d > kWarpAccMaxD), grown on demand
   size_t gacc_cap = 0;     // doubles
+  double* gm_ws = nullptr;  // PDGMRES work space (basis, vectors, scalars), grown on demand
+  size_t gm_ws_cap = 0;     // doubles
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
 
@@ -165,6 +167,8 @@ cudaError_t launch_residual(sld_system s, const double* b, const double* x, doub
                             double* rr_host, double* bb_host);
 // s->gacc with room for `doubles` values (kept, grown on demand)
 cudaError_t ensure_gacc(sld_system s, size_t doubles);
+// s->gm_ws with room for `doubles` values (kept, grown on demand)
+cudaError_t ensure_gmres_ws(sld_system s, size_t doubles);
 // sld_solve_tma.cu
 bool tma_eligible(const Geo& g, bool fp64);
 int launch_solve_tma(sld_system s, SolveArgs& a, const sld_options& o, float* ms, std::string* msg);
