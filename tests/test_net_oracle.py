@@ -121,3 +121,28 @@ def test_param_flatten_roundtrip():
     assert flat.size == sum(27 * ci * co + co for ci, co in N.LAYERS)
     q = N.unflatten(flat)
     assert all(np.array_equal(a, b) for a, b in zip(p, q))
+
+
+def test_pool_and_up_values():
+    """Pooling is the mean of each 2x2x2 block (not the sum) and upsampling
+    repeats each value into its 2x2x2 block: checked cell by cell on random
+    data, and on a constant field (the mean of a constant is the constant)."""
+    rng = _rng(21)
+    x = rng.standard_normal((4, 6, 8, 3))
+    p = N.pool(x)
+    assert p.shape == (2, 3, 4, 3)
+    for z in range(2):
+        for y in range(3):
+            for xx in range(4):
+                blk = x[2 * z:2 * z + 2, 2 * y:2 * y + 2, 2 * xx:2 * xx + 2, :]
+                np.testing.assert_allclose(p[z, y, xx], blk.reshape(-1, 3).mean(axis=0), rtol=1e-14)
+    np.testing.assert_allclose(N.pool(np.full((4, 4, 4, 2), 3.5)), 3.5, rtol=0, atol=0)
+    a = rng.standard_normal((2, 3, 4, 2))
+    u = N.up(a)
+    assert u.shape == (4, 6, 8, 2)
+    for z in range(4):
+        for y in range(6):
+            for xx in range(8):
+                assert np.array_equal(u[z, y, xx], a[z // 2, y // 2, xx // 2])
+    # pooling after upsampling gives the coarse field back
+    np.testing.assert_allclose(N.pool(u), a, rtol=1e-14)

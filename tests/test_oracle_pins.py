@@ -319,3 +319,23 @@ def test_jump_independence(oracle_mod):
     assert max(it_d) <= it_d[0] + 4, it_d
     assert it_p[-1] > 1.3 * it_p[0], it_p
     assert all(a <= b for a, b in zip(it_d, it_p)), (it_d, it_p)
+
+
+def test_restrict_is_z_transpose_times_v(oracle_mod):
+    """oracle.restrict(label, d, v) = Z^T v, with Z the explicit indicator
+    matrix of the labels (dense on a small grid), and with extra dense
+    columns appended; empty labels give exact zeros."""
+    rng = np.random.default_rng(31)
+    n, d, k = 300, 11, 3
+    lab = rng.integers(0, d - 2, n).astype(np.int32)  # labels d-2, d-1 never used
+    v = rng.standard_normal(n)
+    Z = np.zeros((n, d))
+    Z[np.arange(n), lab] = 1.0
+    s = oracle_mod.restrict(lab, d, v)
+    np.testing.assert_allclose(s, Z.T @ v, rtol=1e-13, atol=1e-13)
+    assert s[d - 2] == 0.0 and s[d - 1] == 0.0
+    Zd = rng.standard_normal((n, k))
+    s2 = oracle_mod.restrict(lab, d, v, Zd=Zd)
+    np.testing.assert_allclose(s2, np.concatenate([Z.T @ v, Zd.T @ v]), rtol=1e-12, atol=1e-12)
+    # a mistake that swaps labels or drops cells would change these sums
+    np.testing.assert_allclose(np.sum(s), np.sum(v), rtol=1e-12)
