@@ -88,8 +88,10 @@ def train(net, data, epochs, lr=2e-3, seed=0, log=None, lr_decay=0.5, decay_ever
     return [float(h) for h in hist]
 
 
-def evaluate(net, seeds, n, precision=sld.FP32_IR, tol=1e-9):
-    """Label deflation alone vs label + learned columns on each field."""
+def evaluate(net, seeds, n, precision=sld.FP32_IR, tol=1e-9, auto_labels=False):
+    """Label deflation alone vs label + learned columns on each field; with
+    auto_labels also the automatic (connected-component) labels alone and
+    with the learned columns appended."""
     torch = _torch()
     out = []
     for seed in seeds:
@@ -105,10 +107,23 @@ def evaluate(net, seeds, n, precision=sld.FP32_IR, tol=1e-9):
         _, ku = s.deflation_info()[1:]
         s.solve(x=x, precision=precision, tol=tol)
         _, lrn = s.solve(x=x, precision=precision, tol=tol)
-        out.append({"seed": seed, "plain_its": plain.iterations, "plain_ms": plain.solve_ms,
-                    "learned_its": lrn.iterations, "learned_ms": lrn.solve_ms, "k_used": ku,
-                    "learned_relres": lrn.true_relres, "plain_relres": plain.true_relres,
-                    "net_and_deflation_setup_ms": setup_ms})
+        row = {"seed": seed, "plain_its": plain.iterations, "plain_ms": plain.solve_ms,
+               "learned_its": lrn.iterations, "learned_ms": lrn.solve_ms, "k_used": ku,
+               "learned_relres": lrn.true_relres, "plain_relres": plain.true_relres,
+               "net_and_deflation_setup_ms": setup_ms}
+        if auto_labels:  # the automatic labels (connected components), alone and with the learned columns
+            _, dcc = s.make_labels_cc(P.S, P.tau, P.L)
+            s.build_deflation(dcc)
+            s.solve(x=x, precision=precision, tol=tol)
+            _, cc = s.solve(x=x, precision=precision, tol=tol)
+            net.infer(s)
+            kcc = s.deflation_info()[2]
+            s.solve(x=x, precision=precision, tol=tol)
+            _, ccl = s.solve(x=x, precision=precision, tol=tol)
+            row.update({"auto_d": dcc, "auto_its": cc.iterations, "auto_ms": cc.solve_ms,
+                        "auto_learned_its": ccl.iterations, "auto_learned_ms": ccl.solve_ms,
+                        "auto_learned_k_used": kcc, "auto_learned_relres": ccl.true_relres})
+        out.append(row)
         s.close()
     return out
 
@@ -124,7 +139,11 @@ def summarize(rows):
             "median_plain_ms": med("plain_ms"), "median_learned_ms": med("learned_ms"),
             "median_time_ratio_plain_over_learned": float(np.median(t_gain)),
             "max_learned_relres": max(r["learned_relres"] for r in rows),
-            "fields_with_columns_dropped": int(sum(r["k_used"] == 0 for r in rows))}
+            "fields_with_columns_dropped": int(sum(r["k_used"] == 0 for r in rows)),
+            **({"median_auto_its": med("auto_its"), "median_auto_ms": med("auto_ms"),
+                "median_auto_learned_its": med("auto_learned_its"), "median_auto_learned_ms": med("auto_learned_ms"),
+                "max_auto_learned_relres": max(r["auto_learned_relres"] for r in rows)}
+               if rows and "auto_its" in rows[0] else {})}
 
 
 def save_params(path, params, meta):
@@ -160,7 +179,7 @@ def main(argv=None):
     t0 = time.perf_counter()
     hist = train(net, data, a.epochs, lr=a.lr, log=log)
     t_train = time.perf_counter() - t0
-    rows = evaluate(net, range(EVAL_SEED0, EVAL_SEED0 + a.eval), a.n)
+    rows = evaluate(net, range(EVAL_SEED0, EVAL_SEED0 + a.eval), a.n, auto_labels=True)
     summ = summarize(rows)
     res = {"n": a.n, "train_fields": a.train, "eval_fields": a.eval, "epochs": a.epochs,
            "dataset_s": t_data, "train_s": t_train, "loss_history": hist, "summary": summ, "rows": rows}
