@@ -70,6 +70,24 @@ __device__ __forceinline__ bool grid_barrier(const SyncArgs& sy, unsigned& epoch
   return s_ok != 0;
 }
 
+// Sum of p[k * stride] over k = k0, k0 + step, ... < n, added in that order,
+// the loads issued eight at a time: a long sum then waits for one memory
+// round trip per eight terms instead of one per term (a loop whose trip
+// count is known only at run time otherwise issues each load after the add
+// before it).  Past n the batch reads nothing and adds +0, which leaves the
+// sum unchanged.  For data written by the running kernel: plain loads.
+__device__ __forceinline__ double ordered_sum(const double* p, int64_t stride, int k0, int n, int step) {
+  double t = 0.0;
+  for (int k = k0; k < n; k += 8 * step) {
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = k + u * step < n ? p[(int64_t)(k + u * step) * stride] : 0.0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) t += v[u];
+  }
+  return t;
+}
+
 // ---------------------------------------------------------------------------
 // Loads / stores of CX consecutive cells.  With CX == 4 and all four cells in
 // range the access is one 16-byte vector (float) or two (double); otherwise

@@ -128,9 +128,7 @@ __global__ void k_gm_colsum(const double* __restrict__ part, int pstride, int G,
   if (stop && *stop) return;
   const int col = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   if (col >= ncol) return;
-  const double* p = part + (int64_t)col * pstride;
-  double t = 0.0;
-  for (int c = lane; c < G; c += 32) t += p[c];
+  double t = ordered_sum(part + (int64_t)col * pstride, 1, lane, G, 32);
   t = warp_sum(t);
   if (lane == 0) out[col] = t;
 }

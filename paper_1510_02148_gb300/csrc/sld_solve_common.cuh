@@ -367,9 +367,7 @@ __device__ void phase_reduce_s(const SolveArgs& a, int extra = 0) {
   const int nw = blockDim.x >> 5;
   const int G = a.sy.ncta;
   for (int k = team_rank(a.sy) * nw + warp; k < a.dk + extra; k += G * nw) {
-    const double* col = a.part + (int64_t)k * a.pstride;
-    double t = 0.0;
-    for (int c = lane; c < G; c += 32) t += col[c];
+    double t = ordered_sum(a.part + (int64_t)k * a.pstride, 1, lane, G, 32);
     t = warp_sum(t);
     if (lane == 0) a.s_glob[k] = t;
   }
@@ -382,7 +380,17 @@ __device__ void phase_coarse(const SolveArgs& a, const double* Einv) {
   for (int j = team_rank(a.sy) * nw + warp; j < a.dk; j += a.sy.ncta * nw) {
     const double* row = Einv + (int64_t)j * a.dk;
     double t = 0.0;
-    for (int k = lane; k < a.dk; k += 32) t += __ldg(row + k) * a.s_glob[k];
+    for (int k0 = lane; k0 < a.dk; k0 += 4 * 32) {  // four products' loads at a time
+      double e[4], v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int k = k0 + 32 * u;
+        e[u] = k < a.dk ? __ldg(row + k) : 0.0;
+        v[u] = k < a.dk ? a.s_glob[k] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) t += e[u] * v[u];
+    }
     t = warp_sum(t);
     if (lane == 0) a.y_glob[j] = t;
   }
@@ -395,8 +403,7 @@ __device__ void cta_scalar2(const SolveArgs& a, int slot0, int slot1, double* re
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (warp < 2) {
     const double* col = a.part + (int64_t)(a.dk + (warp ? slot1 : slot0)) * a.pstride;
-    double t = 0.0;
-    for (int c = lane; c < a.sy.ncta; c += 32) t += col[c];
+    double t = ordered_sum(col, 1, lane, a.sy.ncta, 32);
     t = warp_sum(t);
     if (lane == 0) red[40 + warp] = t;
   }
@@ -453,11 +460,14 @@ __device__ void solve_body(const SolveArgs& a, double* acc, double* Yd, T* Y, do
   // target of the last step, whether it was relative (not the 0.3 tol
   // floor), the last verified |d| / |x| (reported at exit).  Every thread
   // reads it after a CTA barrier; thread 0 writes it after another one.
-  enum { kTgtPrev = 0, kRelPrev, kFwdRel, kFwdSteps, kDdPrev, kRrPrev, kFsCount };
+  // kEst: the estimate reported at exit (the last verified |d| / |x|, or the
+  // contraction estimate of a step the fast rule accepted).
+  enum { kTgtPrev = 0, kRelPrev, kFwdRel, kFwdSteps, kDdPrev, kRrPrev, kEst, kFsCount };
   __shared__ double fs[kFsCount];
   if (threadIdx.x == 0) {
     for (int k = 0; k < kFsCount; ++k) fs[k] = 0.0;
     fs[kFwdRel] = -1.0;
+    fs[kEst] = -1.0;
   }
   int its = 0, outer = 0, status = 0;
   bool converged = false;
@@ -525,9 +535,13 @@ __device__ void solve_body(const SolveArgs& a, double* acc, double* Yd, T* Y, do
       const double tgt2n = fmin(fmax(a.inner_tol * a.inner_tol * rr_outer, floor2), kMinCut2 * rr_outer);
       __syncthreads();  // every thread has read fs
       if (threadIdx.x == 0) {
-        if (verified) fs[kFwdRel] = drel;
+        if (verified) fs[kFwdRel] = fs[kEst] = drel;
         if (res_ok) fs[kFwdSteps] += 1.0;
-        if (strong && !verified) fs[kFwdRel] = dd / sqrt(fs[kDdPrev] * xx);
+        if (strong) {
+          const double est = dd / sqrt(fs[kDdPrev] * xx);
+          if (!verified) fs[kFwdRel] = est;
+          fs[kEst] = est;
+        }
         fs[kDdPrev] = dd;
         fs[kRrPrev] = rr_outer;
         fs[kTgtPrev] = tgt2n;
@@ -579,7 +593,7 @@ __device__ void solve_body(const SolveArgs& a, double* acc, double* Yd, T* Y, do
     a.out[kOutBB] = bb;
     a.out[kOutStatus] = failed ? -1.0 : (status ? (double)status : (converged ? 0.0 : (double)SLD_ERR_NOT_CONVERGED));
     a.out[kOutRecRR] = rec_rr;
-    a.out[kOutFwd] = fs[kFwdRel];
+    a.out[kOutFwd] = fs[kEst];
     a.out[kOutEndNs] = (double)global_ns();
   }
 }
