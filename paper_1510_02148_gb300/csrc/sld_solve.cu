@@ -182,7 +182,8 @@ __device__ void sweep_A(const SolveArgs& a, const Sm<T>& sm, const T* zb, const 
   la.init(a.lab_L);
   double dgam = 0.0;
   const int tr = team_rank(a.sy);
-  const int64_t t0 = a.ntiles * tr / a.sy.ncta, t1 = a.ntiles * (tr + 1) / a.sy.ncta;
+  int64_t t0, t1;
+  tile_range(a, tr, &t0, &t1);
   for (int64_t t = t0; t < t1;) {
     const int64_t ct = t / g.nz;
     const int z0 = (int)(t % g.nz);
@@ -396,7 +397,8 @@ __device__ void sweep_B(const SolveArgs& a, const Sm<T>& sm, const T* p, T* zb, 
   const T* Y = sm.Y;
   double drho = 0.0, drr = 0.0;
   const int tr = team_rank(a.sy);
-  const int64_t t0 = a.ntiles * tr / a.sy.ncta, t1 = a.ntiles * (tr + 1) / a.sy.ncta;
+  int64_t t0, t1;
+  tile_range(a, tr, &t0, &t1);
   for (int64_t t = t0; t < t1;) {
     const int64_t ct = t / g.nz;
     const int z0 = (int)(t % g.nz);

@@ -27,6 +27,29 @@
 namespace sld {
 namespace {
 
+// The plane-tiles [*t0, *t1) of team rank tr.  Tiles run column by column
+// (nz planes per column), and a rank reads two halo planes more for every
+// column it touches, so the split balances plane loads, nz + 2 per column,
+// rather than tiles: a rank whose range crosses a column boundary gets two
+// tiles fewer.  With fewer than four tiles per rank the split is by tiles
+// (it keeps every range non-empty).
+__device__ __forceinline__ void tile_range(const SolveArgs& a, int tr, int64_t* t0, int64_t* t1) {
+  const int64_t G = a.sy.ncta, nz = a.g.nz;
+  if (a.ntiles < 4 * G || a.ntiles % nz != 0) {
+    *t0 = a.ntiles * tr / G;
+    *t1 = a.ntiles * (tr + 1) / G;
+    return;
+  }
+  const int64_t per = nz + 2, units = a.ntiles / nz * per;
+  auto bound = [&](int64_t r) {
+    const int64_t p = units * r / G;  // position in plane loads
+    const int64_t j = p / per, q = p - j * per;
+    return j * nz + (q < 1 ? 0 : (q - 1 < nz ? q - 1 : nz));
+  };
+  *t0 = bound(tr);
+  *t1 = bound(tr + 1);
+}
+
 // Block-wide sum of one double per thread (fixed order); result to all threads.
 __device__ double block_sum(double v, double* red) {
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;

@@ -260,7 +260,8 @@ __device__ bool sweep_tma(const SolveArgs& a, const Maps& mp, const Ring<S>& rg,
     for (int k = tid; k < C::kAcc * d; k += blockDim.x) sacc[k] = 0.0;
   }
   const int tr = team_rank(a.sy);
-  const int64_t t0 = a.ntiles * tr / a.sy.ncta, t1 = a.ntiles * (tr + 1) / a.sy.ncta;
+  int64_t t0, t1;
+  tile_range(a, tr, &t0, &t1);
   const uint64_t first = gitem;
   uint64_t released = gitem;  // items below this are free
   uint64_t issued = gitem;    // thread 0 only
