@@ -43,7 +43,7 @@ BYTES_ITER_BF16 = 52   # A: z, p_old, 3 BF16 faces, label, p_new  B: p, label, 3
 # ncu capture of a 300-iteration launch on this workload; the traffic of a
 # full launch is this ratio times its algorithmic bytes.  Must be re-measured
 # (or set to None) whenever that kernel changes.
-TRAFFIC_RATIO_FP32 = 1.095
+TRAFFIC_RATIO_FP32 = 1.084
 
 
 def _peaks():
@@ -73,6 +73,12 @@ class ClockSampler:
                  "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            # nvidia-smi's start-up (NVML initialisation) can hold up the
+            # CUDA calls of this process for a large fraction of a second:
+            # let it print its first sample before the timed region opens
+            t0 = time.perf_counter()
+            while not self.lines and self.proc.poll() is None and time.perf_counter() - t0 < 10.0:
+                time.sleep(0.01)
         except (OSError, FileNotFoundError):
             self.proc = None
         return self
