@@ -507,6 +507,35 @@ def profile_solve(args):
     return 0 if info.status in (sld.OK, sld.ERR_NOT_CONVERGED) else 1
 
 
+def profile_batch(args):
+    """One batched launch (no autotune trials: a fixed shape of four CTAs per
+    SM) over 16 layered cubes with sides 64..128 -- the batch workload's
+    recipe on a narrower side range -- so that a profiler captures exactly
+    one launch of the batched solve kernel."""
+    import torch
+    from paper_1510_02148_gb300 import _build, sld, workloads as W
+    _build.build()
+    sld.load()
+    probs = W.batch(16, side_range=(64, 128), seed=1)
+    systems = []
+    for P in probs:
+        s = sld.System(torch.from_numpy(P.K.reshape(-1)).cuda(), None, P.bc_type, P.bc_value, shape=P.shape)
+        s.make_labels(P.S, P.tau, P.L)
+        s.build_deflation(P.d)
+        systems.append(s)
+    xs = [torch.empty(P.n, dtype=torch.float64, device="cuda") for P in probs]
+    kw = {"maxiter": args.maxiter} if args.maxiter > 0 else {}
+    bt = sld.Batch(systems, precision=sld.FP32_IR, ctas_per_sm=4, **kw)
+    _, infos = bt.solve(xs=xs, raise_on_error=False)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_batch": len(probs), "cells": sum(P.n for P in probs),
+                      "iterations": [i.iterations for i in infos], "solve_ms": infos[0].solve_ms}), flush=True)
+    bt.close()
+    for s in systems:
+        s.close()
+    return 0 if all(i.status in (sld.OK, sld.ERR_NOT_CONVERGED) for i in infos) else 1
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -528,13 +557,18 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--profile-solve", choices=["fp64", "fp32_ir", "bf16"], default=None,
                     help="set up the workload and run one solve (for profiler captures); no timing line")
-    ap.add_argument("--maxiter", type=int, default=0, help="with --profile-solve: inner iteration cap")
+    ap.add_argument("--maxiter", type=int, default=0,
+                    help="with --profile-solve / --profile-batch: inner iteration cap")
+    ap.add_argument("--profile-batch", action="store_true",
+                    help="set up 16 layered cubes and run one batched launch (for profiler captures); no timing line")
     ap.add_argument("--shape", type=int, nargs=3, default=None, help="with --profile-solve: grid nx ny nz")
     ap.add_argument("--profile-workload", choices=["lognormal", "inclusions"], default="lognormal",
                     help="with --profile-solve: the lognormal point-source field or the inclusion field")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_batch:
+        return profile_batch(args)
     if args.profile_solve:
         return profile_solve(args)
 

@@ -784,21 +784,48 @@ sld_status sld_batch_create(sld_system* systems, int count, const sld_options* o
       sld::batch_free(&trial);
     }
   }
-  // two more candidates: teams rebalanced from the CTA-time each system took
-  // in the last timed launch (its team's CTAs x its time in the kernel), the
-  // same launch shape; the second from the first's measurement
-  for (int round = 0; round < 2 && o.ctas_per_sm <= 0 && bt->plan.exec; ++round) {
-    std::vector<double> wk(count);
-    bool okw = true;
-    for (int k = 0; k < count && okw; ++k) {
+  // more candidates, teams rebalanced from measurement: each system's time
+  // in the kernel (its team's first to last moment) in every timed launch
+  // so far.  Where a system has been timed with two team sizes at least 25 %
+  // apart, its time is modelled as a / t + b (b: the part more CTAs do not
+  // shorten, such as its grid barriers), kept only if b is under 30 % of its
+  // last time (the times are noisy, and a fit that calls most of the time
+  // fixed starves the system of CTAs), else as proportional to 1 / t.  Up to
+  // six rounds, ending after two that do not beat the best plan by 0.5 %;
+  // the best is kept.
+  std::vector<std::vector<std::pair<double, double>>> hist(count);  // (team size, ns) per timed launch
+  auto record = [&]() {
+    for (int k = 0; k < count; ++k) {
       double out[sld::kOutCount];
-      okw = cudaMemcpy(out, systems[k]->out, sizeof(out), cudaMemcpyDeviceToHost) == cudaSuccess;
-      wk[k] = std::max(out[sld::kOutEndNs] - out[sld::kOutStartNs], 1.0) * last_teams[k];
+      if (cudaMemcpy(out, systems[k]->out, sizeof(out), cudaMemcpyDeviceToHost) != cudaSuccess) return false;
+      hist[k].push_back({last_teams[k], std::max(out[sld::kOutEndNs] - out[sld::kOutStartNs], 1.0)});
+    }
+    return true;
+  };
+  int stale = 0;
+  for (int round = 0; round < 6 && stale < 2 && o.ctas_per_sm <= 0 && bt->plan.exec; ++round) {
+    if (!record()) break;
+    std::vector<double> ak(count), bk(count, 0.0);
+    for (int k = 0; k < count; ++k) {
+      const auto& h = hist[k];
+      const auto last = h.back();
+      ak[k] = last.second * last.first;  // proportional to 1 / t
+      for (size_t i = h.size() - 1; i-- > 0;) {  // the latest earlier launch with another team size
+        if (h[i].first == last.first) continue;
+        if (std::fabs(h[i].first - last.first) < 0.25 * std::max(h[i].first, last.first)) break;
+        const double u1 = 1.0 / last.first, u2 = 1.0 / h[i].first;
+        const double a = (last.second - h[i].second) / (u1 - u2), b = last.second - a * u1;
+        if (a > 0.0 && b >= 0.0 && b <= 0.3 * last.second) {
+          ak[k] = a;
+          bk[k] = b;
+        }
+        break;
+      }
     }
     sld::BatchPlan trial;
     std::string msg;
-    if (!okw || sld::batch_build(bt->sys.data(), count, o, bt->plan.per_sm, 1.0, wk.data(), bt->plan.cx, bt->stream,
-                                 &trial, &msg) != SLD_OK) {
+    if (sld::batch_build(bt->sys.data(), count, o, bt->plan.per_sm, 1.0, ak.data(), bt->plan.cx, bt->stream, &trial,
+                         &msg, bk.data()) != SLD_OK) {
       sld::batch_free(&trial);
       break;
     }
@@ -813,6 +840,7 @@ sld_status sld_batch_create(sld_system* systems, int count, const sld_options* o
     }
     times += " [rebalanced " + std::to_string(round + 1) + ": " + std::to_string(ms).substr(0, 7) + " ms]";
     for (int k = 0; k < count; ++k) last_teams[k] = trial.teams[k];
+    stale = ms < 0.995f * best_ms ? 0 : stale + 1;
     if (ms < best_ms) {
       sld::batch_free(&bt->plan);
       bt->plan = trial;

@@ -227,9 +227,10 @@ struct BatchPlan {
   cudaGraphExec_t exec = nullptr;
   int teams[4096];
 };
-// cost: measured CTA-time per system (count values; teams by min-max of
-// cost / team), or nullptr for teams proportional to n^expo
+// cost: modelled CTA-time per system (count values; teams by min-max of
+// cost / team + fixed, fixed = the part of a system's time that more CTAs do
+// not shorten, nullptr = 0), or nullptr for teams proportional to n^expo
 int batch_build(sld_system* sys, int count, const sld_options& o, int per_sm, double expo, const double* cost,
-                int cx, cudaStream_t stream, BatchPlan* plan, std::string* msg);
+                int cx, cudaStream_t stream, BatchPlan* plan, std::string* msg, const double* fixed = nullptr);
 void batch_free(BatchPlan* plan);
 }  // namespace sld

@@ -947,11 +947,12 @@ void batch_free(BatchPlan* p) {
 // partial-sum row.  Without a measurement, system k's share is proportional
 // to n_k^expo.  With one (cost: the CTA-time each system took in an earlier
 // launch, its team's CTAs x its time in the kernel), the CTAs are dealt out
-// to minimise the slowest system's modelled time T_k(t) = cost_k / t:
-// every system starts with one CTA and each further CTA goes to the
-// currently slowest system (optimal for these decreasing convex times).
+// to minimise the slowest system's modelled time
+// T_k(t) = cost_k / t + fixed_k: every system starts with one CTA and each
+// further CTA goes to the currently slowest system (optimal for these
+// decreasing convex times).
 int batch_build(sld_system* sys, int count, const sld_options& o, int per_sm, double expo, const double* cost,
-                int cx, cudaStream_t stream, BatchPlan* p, std::string* msg) {
+                int cx, cudaStream_t stream, BatchPlan* p, std::string* msg, const double* fixed) {
   sld_system s0 = sys[0];
   p->stream = stream;
   p->count = count;
@@ -1012,7 +1013,7 @@ int batch_build(sld_system* sys, int count, const sld_options& o, int per_sm, do
   if (cost) {  // min-max over the modelled times, greedy
     for (int k = 0; k < count; ++k) p->teams[k] = 1;
     used = count;
-    auto T = [&](int k, int t) { return std::max(cost[k], 1e-9) / t; };
+    auto T = [&](int k, int t) { return std::max(cost[k], 1e-9) / t + (fixed ? fixed[k] : 0.0); };
     std::vector<std::pair<double, int>> heap;
     for (int k = 0; k < count; ++k) heap.push_back({T(k, 1), k});
     std::make_heap(heap.begin(), heap.end());
