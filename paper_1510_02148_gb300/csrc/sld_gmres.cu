@@ -46,14 +46,16 @@ enum { GM_PRECOND = 0, GM_RESID = 1, GM_APPLY = 2, GM_COPY = 3, GM_BAPPLY = 4 };
 
 // w = op(v) at every cell, and this CTA's row of Z^T w.
 //   GM_PRECOND: v is the raw next basis vector; v_j = v / sqrt(*norm2) is
-//               written to vout and w = A M^{-1} v_j
+//               written to vout and w = A M^{-1} v_j (with u = M^{-1} v given:
+//               w = A u / sqrt(*norm2), the scaling applied once per cell)
 //   GM_RESID:   w = b - A v        GM_APPLY: w = A v        GM_COPY: w = v (not stored)
 //   GM_BAPPLY:  w = A M^{-1} v (the right-preconditioned operator B)
 template <int MODE, bool WACC>
 __global__ void __launch_bounds__(kGT) k_gm_apply(SolveArgs a, const double* __restrict__ v,
                                                   const double* __restrict__ norm2, double* __restrict__ vout,
                                                   double* __restrict__ w, double* __restrict__ part,
-                                                  const int* __restrict__ stop = nullptr) {
+                                                  const int* __restrict__ stop = nullptr,
+                                                  const double* __restrict__ u = nullptr) {
   if (stop && *stop) return;  // the device Givens step ended the cycle
   extern __shared__ double sacc[];
   const int d = a.d;
@@ -75,7 +77,8 @@ __global__ void __launch_bounds__(kGT) k_gm_apply(SolveArgs a, const double* __r
   auto cell = [&](const CellWalk& cw, double& wv, int& l) {
     const int64_t i = cw.i;
     if constexpr (MODE == GM_PRECOND) {
-      wv = apply64(a, cw, [&](int64_t j, int64_t) { return (v[j] * sc) * a.invdiag64[j]; });
+      if (u) wv = sc * apply64(a, cw, [&](int64_t j, int64_t) { return u[j]; });
+      else wv = apply64(a, cw, [&](int64_t j, int64_t) { return (v[j] * sc) * a.invdiag64[j]; });
       vout[i] = v[i] * sc;
     } else if constexpr (MODE == GM_RESID) {
       wv = a.b[i] - apply64(a, cw, [&](int64_t j, int64_t) { return v[j]; });
@@ -200,7 +203,9 @@ __global__ void __launch_bounds__(kGT) k_gm_dots(int64_t n, const double* __rest
 __global__ void __launch_bounds__(kGT) k_gm_orth(int64_t n, const double* __restrict__ V, int nv,
                                                  const double* __restrict__ h, const double* w, double* out,
                                                  double* __restrict__ part, int pstride, int norm_col,
-                                                 const int* __restrict__ stop = nullptr) {
+                                                 const int* __restrict__ stop = nullptr,
+                                                 const double* __restrict__ invd = nullptr,
+                                                 double* __restrict__ uout = nullptr) {
   if (stop && *stop) return;
   __shared__ double hs[kGMaxBasis];
   __shared__ double red[kGT / 32];
@@ -212,6 +217,7 @@ __global__ void __launch_bounds__(kGT) k_gm_orth(int64_t n, const double* __rest
 #pragma unroll 4
     for (int k = 0; k < nv; ++k) t -= hs[k] * V[(int64_t)k * n + i];
     out[i] = t;
+    if (uout) uout[i] = t * invd[i];  // M^{-1} of the next raw vector, for its apply
     nn += t * t;
   }
   if (norm_col < 0) return;
@@ -326,9 +332,10 @@ int run_gmres(sld_system s, const double* b, int m, int deflate, double tol, int
   const int ps = a.pstride;
   double* part = a.part;
   // work space, kept by the handle between calls: the basis (m + 1) n, w,
-  // raw, x~ (n each), small vectors, the device scalars and Givens state
+  // raw, x~, M^{-1} raw (n each), small vectors, the device scalars and
+  // Givens state
   const size_t small = (size_t)4 * (d + 1) + kGMaxBasis;
-  const size_t scal_off = ((size_t)(m + 4) * n + small + 31) / 32 * 32;  // doubles, 256-byte aligned
+  const size_t scal_off = ((size_t)(m + 5) * n + small + 31) / 32 * 32;  // doubles, 256-byte aligned
   const size_t gs_off = scal_off + (sizeof(Scal) + 255) / 256 * 32;
   const size_t need = gs_off + (sizeof(GivensState) + 255) / 256 * 32;
   cudaError_t e = ensure_gmres_ws(s, need);
@@ -343,8 +350,8 @@ int run_gmres(sld_system s, const double* b, int m, int deflate, double tol, int
   GivensState* gs = reinterpret_cast<GivensState*>(s->gm_ws + gs_off);
   std::unique_ptr<GivensState> hgs_own(new GivensState());
   GivensState* hgs = hgs_own.get();
-  double *w = work, *raw = w + n, *xt = raw + n;
-  double *sv = xt + n, *y = sv + (d + 1), *y0 = y + (d + 1), *y1 = y0 + (d + 1), *ud = y1 + (d + 1);
+  double *w = work, *raw = w + n, *xt = raw + n, *um = xt + n;  // um = M^{-1} raw
+  double *sv = um + n, *y = sv + (d + 1), *y0 = y + (d + 1), *y1 = y0 + (d + 1), *ud = y1 + (d + 1);
   const size_t smem = sizeof(double) * (size_t)(wacc ? kGT / 32 : 1) * (size_t)std::max(d, 1);
   // colsum / gemv: one warp per column (row), 8 warps per block
   auto cols = [&](int ncol) { return dim3((unsigned)((ncol + 7) / 8)); };
@@ -357,10 +364,10 @@ int run_gmres(sld_system s, const double* b, int m, int deflate, double tol, int
     k_gm_gemv<<<cols(d), 256, 0, st>>>(d, a.Einv, sv, yout);
   };
   auto apply = [&](int mode, const double* v, const double* nrm2, double* vout, double* wout,
-                   const int* stp = nullptr) {
+                   const int* stp = nullptr, const double* uin = nullptr) {
 #define GM_LAUNCH(MODE)                                                                              \
-  (wacc ? k_gm_apply<MODE, true><<<G, kGT, smem, st>>>(a, v, nrm2, vout, wout, part, stp)             \
-        : k_gm_apply<MODE, false><<<G, kGT, smem, st>>>(a, v, nrm2, vout, wout, part, stp))
+  (wacc ? k_gm_apply<MODE, true><<<G, kGT, smem, st>>>(a, v, nrm2, vout, wout, part, stp, uin)        \
+        : k_gm_apply<MODE, false><<<G, kGT, smem, st>>>(a, v, nrm2, vout, wout, part, stp, uin))
     switch (mode) {
       case GM_PRECOND: GM_LAUNCH(GM_PRECOND); break;
       case GM_RESID: GM_LAUNCH(GM_RESID); break;
@@ -407,7 +414,7 @@ int run_gmres(sld_system s, const double* b, int m, int deflate, double tol, int
       coarse(y);
       k_gm_defl<<<G, kGT, 0, st>>>(a, y, w);
     }
-    k_gm_orth<<<G, kGT, 0, st>>>(n, V, 0, sc->h1, w, raw, part, ps, 0);
+    k_gm_orth<<<G, kGT, 0, st>>>(n, V, 0, sc->h1, w, raw, part, ps, 0, nullptr, a.invdiag64, um);
     colsum(1, &sc->nn);
     if (!fetch()) break;
     const double beta = std::sqrt(hs.nn);
@@ -432,7 +439,7 @@ int run_gmres(sld_system s, const double* b, int m, int deflate, double tol, int
     for (int j = 0; j < steps; ++j) {
       const int nv = j + 1;
       // v_j = raw / |raw|, w = P1 A M^{-1} v_j, h1 = V^T w
-      apply(GM_PRECOND, raw, &sc->nn, V + (size_t)j * n, w, stp);
+      apply(GM_PRECOND, raw, &sc->nn, V + (size_t)j * n, w, stp, um);
       if (d > 0) {
         colsum(d, sv, stp);
         k_gm_gemv<<<cols(d), 256, 0, st>>>(d, a.Einv, sv, y, stp);
@@ -444,7 +451,7 @@ int run_gmres(sld_system s, const double* b, int m, int deflate, double tol, int
       k_gm_orth<<<G, kGT, 0, st>>>(n, V, nv, sc->h1, w, w, part, ps, -1, stp);
       k_gm_dots<<<dim3(G, (nv + kGDots - 1) / kGDots), kGT, 0, st>>>(n, V, nv, w, part, ps, stp);
       colsum(nv, sc->h2, stp);
-      k_gm_orth<<<G, kGT, 0, st>>>(n, V, nv, sc->h2, w, raw, part, ps, 0, stp);
+      k_gm_orth<<<G, kGT, 0, st>>>(n, V, nv, sc->h2, w, raw, part, ps, 0, stp, a.invdiag64, um);
       colsum(1, &sc->nn, stp);
       k_gm_givens<<<1, 32, 0, st>>>(sc->h1, sc->h2, &sc->nn, gs, j, tol * bnorm, j + 1 == steps ? 1 : 0);
     }
