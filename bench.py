@@ -361,9 +361,16 @@ def bench_batched(sld, torch, reps=3):
         _, i1 = s.solve(x=x, precision=sld.FP32_IR)
         seq += i1.solve_ms
     cells = sum(P.n for P in probs)
-    alg = sum(P.n * (64 * i.iterations + BYTES_OUTER * i.outer_steps) for P, i in zip(probs, infos))
+    # the batched kernel streams the single solve's arrays (16-bit labels): 60 B per cell-iteration
+    alg = sum(P.n * (BYTES_ITER_FP32 * i.iterations + BYTES_OUTER * i.outer_steps) for P, i in zip(probs, infos))
+    peak, peak_kind = _peaks()
+    gbs = alg / (ms * 1e-3) / 1e9
     out = {"systems": len(probs), "cells": cells, "ms": ms, "solves_per_s": len(probs) / (ms * 1e-3),
-           "alg_gbs": alg / (ms * 1e-3) / 1e9, "iterations_total": sum(i.iterations for i in infos),
+           "alg_gbs": gbs,
+           "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                        "traffic": None, "bytes_per_cell_iter": BYTES_ITER_FP32, "peak_kind": peak_kind,
+                        "kernel": "k_solve_tma_batch_p<float, float, 8, 3, 1> (one launch, all systems)"},
+           "iterations_total": sum(i.iterations for i in infos),
            "max_true_relres": max(i.true_relres for i in infos),
            "one_at_a_time_ms": seq, "speedup_vs_one_at_a_time": seq / ms, "plan": bt.describe(),
            "plan_and_tune_s": plan_s}
