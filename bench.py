@@ -514,6 +514,37 @@ def profile_solve(args):
     return 0 if info.status in (sld.OK, sld.ERR_NOT_CONVERGED) else 1
 
 
+def profile_net(args):
+    """The deflation-vector network on a cubic grid (side --shape's nx,
+    default 64) with the fixed initial weights of the training driver: one
+    forward pass, then --net-steps training steps (forward, subspace loss
+    and gradients, Adam) against synthetic targets -- for profiler captures
+    of the convolution kernels."""
+    import torch
+    from paper_1510_02148_gb300 import _build, learned, sld, workloads as W
+    _build.build()
+    sld.load()
+    n = args.shape[0] if args.shape else 64
+    P = W.learned_field(0, n=n)
+    K = torch.from_numpy(P.K.reshape(-1)).cuda()
+    g = torch.Generator(device="cpu").manual_seed(0)
+    V = torch.randn((P.n, 8), generator=g, dtype=torch.float32).cuda()
+    D = torch.ones(P.n, dtype=torch.float64, device="cuda")
+    net = sld.Net((n, n, n))
+    net.set_params(learned.init_params(0))
+    out = torch.empty((P.n, 8), dtype=torch.float32, device="cuda")
+    net.forward(K, out=out)
+    losses = []
+    for step in range(1, args.net_steps + 1):
+        net.forward(K, keep=True)
+        losses.append(net.loss_backward(V, D))
+        net.adam(1e-3, step)
+    torch.cuda.synchronize()
+    net.close()
+    print(json.dumps({"profile_net": n, "steps": args.net_steps, "losses": losses}), flush=True)
+    return 0
+
+
 def profile_batch(args):
     """One batched launch (no autotune trials: a fixed shape of four CTAs per
     SM) over 16 layered cubes with sides 64..128 -- the batch workload's
@@ -566,6 +597,9 @@ def main():
                     help="set up the workload and run one solve (for profiler captures); no timing line")
     ap.add_argument("--maxiter", type=int, default=0,
                     help="with --profile-solve / --profile-batch: inner iteration cap")
+    ap.add_argument("--profile-net", action="store_true",
+                    help="run the deflation-vector network (forward, training steps) on a cube (for profiler captures)")
+    ap.add_argument("--net-steps", type=int, default=3, help="with --profile-net: training steps")
     ap.add_argument("--profile-batch", action="store_true",
                     help="set up 16 layered cubes and run one batched launch (for profiler captures); no timing line")
     ap.add_argument("--shape", type=int, nargs=3, default=None, help="with --profile-solve: grid nx ny nz")
@@ -576,6 +610,8 @@ def main():
         return run_reference(args)
     if args.profile_batch:
         return profile_batch(args)
+    if args.profile_net:
+        return profile_net(args)
     if args.profile_solve:
         return profile_solve(args)
 
