@@ -111,7 +111,13 @@ typedef struct {
                              shrinking: the test then gives up (the residual test
                              stands) once a verified correction fails to halve
                              the previous one, or after 4 steps past the residual
-                             test.  0 = 100 * tol (the default); < 0 = off (the
+                             test.  With SLD_BF16COEF_IR a test that gave up
+                             above fwd_tol hands the solve on: sld_solve goes on
+                             from its x with SLD_FP32_IR refinement steps (FP32
+                             faces made on first use), and sld_result counts
+                             both parts (iterations, outer steps, solve_ms; the
+                             estimate is the FP32 part's).
+                             0 = 100 * tol (the default); < 0 = off (the
                              residual test alone: fewer steps on high-contrast
                              fields, larger error along the smallest
                              eigenvalues). */

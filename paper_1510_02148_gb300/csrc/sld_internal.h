@@ -84,6 +84,7 @@ struct SolveArgs {
   int maxiter, max_outer;
   int fp64;               // 1: inner in FP64, single inner solve + finalisation
   int bf16;               // 1: inner faces stored as BF16
+  int warm;               // 1: x holds an earlier solve's result, refined further
 };
 
 enum {
@@ -205,8 +206,10 @@ int run_rdgmres(sld_system s, const double* b, int m, int nd, double tol, int ma
                 std::string* msg);
 // sld_solve.cu
 void fill_args(sld_system s, const double* b_dev, const sld_options& o, SolveArgs* a);
+// warm: keep x and refine it (no zeroing, and the first refinement step is
+// not taken as the exact coarse solution by the forward-error test)
 int run_solve(sld_system s, const double* b_dev, const sld_options& o, sld_result* res,
-              std::string* msg);  // returns sld_status
+              std::string* msg, bool warm = false);  // returns sld_status
 
 // A batched solve: one cooperative launch over all systems, each solved by
 // its own team of CTAs, captured with its state resets in a CUDA graph.

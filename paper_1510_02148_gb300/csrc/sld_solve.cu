@@ -779,16 +779,19 @@ void fill_args(sld_system s, const double* b_dev, const sld_options& o, SolveArg
   a.maxiter = o.maxiter;
   a.max_outer = fp64 ? 1 : o.max_outer;
   a.fp64 = fp64 ? 1 : 0;
+  a.warm = 0;
 }
 
-int run_solve(sld_system s, const double* b_dev, const sld_options& o, sld_result* res, std::string* msg) {
+int run_solve(sld_system s, const double* b_dev, const sld_options& o, sld_result* res, std::string* msg,
+              bool warm) {
   const int64_t n = s->g.n;
   const bool fp64 = o.precision == SLD_FP64;
   const bool bf16 = o.precision == SLD_BF16COEF_IR;
   SolveArgs a;
   fill_args(s, b_dev, o, &a);
-  // x = 0; the inner state is set by the first refinement step
-  cudaMemsetAsync(s->x, 0, sizeof(double) * n, s->stream);
+  a.warm = warm && !fp64 ? 1 : 0;
+  // x = 0 (unless warm); the inner state is set by the first refinement step
+  if (!a.warm) cudaMemsetAsync(s->x, 0, sizeof(double) * n, s->stream);
   cudaMemsetAsync(s->xh, 0, sizeof(double) * s->nvec, s->stream);
   cudaMemsetAsync(s->bar, 0, 64, s->stream);
   cudaMemsetAsync(s->out, 0, sizeof(double) * kOutCount, s->stream);

@@ -539,7 +539,8 @@ __device__ void solve_body(const SolveArgs& a, double* acc, double* Yd, T* Y, do
       // shrinking: the test then ends at the residual test's result once a
       // verified correction fails to halve the previous verified one, or
       // after kMaxFwdSteps steps past the residual test (the reported
-      // estimate keeps the last verified correction).
+      // estimate keeps the last verified correction).  A warm start (x
+      // refined further) has no exact first step.
       const bool verified = outer >= 3 && fs[kRelPrev] != 0.0 && rr_outer <= 4.0 * fs[kTgtPrev];
       const double drel = xx > 0.0 ? sqrt(dd / xx) : 0.0;
       // A step that cut the residual at least 1e3-fold and shrank the
@@ -548,7 +549,7 @@ __device__ void solve_body(const SolveArgs& a, double* acc, double* Yd, T* Y, do
       const bool strong = outer >= 3 && fs[kDdPrev] > 0.0 && rr_outer <= 1e-6 * fs[kRrPrev] &&
                           dd <= 1e-6 * fs[kDdPrev] && xx > 0.0 &&
                           dd / sqrt(fs[kDdPrev] * xx) <= 0.1 * a.fwd_tol;
-      const bool fwd_ok = a.fwd_tol < 0.0 || outer == 1 || (verified && drel <= a.fwd_tol) || strong;
+      const bool fwd_ok = a.fwd_tol < 0.0 || (outer == 1 && !a.warm) || (verified && drel <= a.fwd_tol) || strong;
       const bool stalled = res_ok && ((verified && fs[kFwdRel] >= 0.0 && drel > 0.5 * fs[kFwdRel]) ||
                                       fs[kFwdSteps] >= (double)kMaxFwdSteps);
       // next inner target: inner_tol relative, floored at 0.3 tol ||b||, and

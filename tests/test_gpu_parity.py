@@ -349,6 +349,37 @@ def test_forward_error_test_of_the_refinement(sld, oracle_mod):
     s.close()
 
 
+def test_bf16_hands_on_to_fp32_refinement(sld, oracle_mod):
+    """A 128x128x64 inclusion field (4x4x4 subdomains x 3 levelsets) on which
+    the BF16 coefficients do not resolve the slowest modes: the BF16
+    refinement's forward-error test gives up above fwd_tol (4.4e-7 from a
+    tight FP64 solution, measured), so sld_solve goes on from that x with
+    FP32-inner refinement steps.  The result meets the 2-norm bar against
+    the exact discrete solution and reports an estimate within fwd_tol; the
+    iterations count both parts."""
+    P = W.inclusion_field(128, 128, 64, S=(4, 4, 4), a_range=(4, 24))[0]
+    A, lab = _oracle_setup(oracle_mod, P)
+    # the reference stops at 1e-11: pushed to 1e-13 the oracle's own FP64
+    # DEF1 iteration breaks down on this field (after 3269 iterations, true
+    # residual 8e-6), at 1e-11 it converges (true residual 1e-11)
+    tight = oracle_mod.dpcg(A, lab, P.d, tol=1e-11)
+    assert tight.status == 0
+    assert np.linalg.norm(A.b - A.spmv(tight.x)) <= 1e-10 * np.linalg.norm(A.b)
+    s = sld.from_problem(P)
+    x0, i0 = s.solve(precision=sld.BF16COEF_IR, fwd_tol=-1.0)
+    x1, i1 = s.solve(precision=sld.BF16COEF_IR)
+    x32, i32 = s.solve(precision=sld.FP32_IR)
+    e0, e1, e32 = (_relerr(v, tight.x) for v in (x0, x1, x32))
+    print(f"incl128 bf16: residual test only {e0:.2e} ({i0.iterations} its); with the forward-error test and "
+          f"the FP32 hand-on {e1:.2e} ({i1.outer_steps} steps, {i1.iterations} its, estimate "
+          f"{i1.fwd_err_estimate:.2e}); fp32 inner alone {e32:.2e} ({i32.iterations} its)")
+    assert i1.true_relres <= 1e-9
+    assert e1 <= 1e-7 and e32 <= 1e-7
+    assert 0.0 <= i1.fwd_err_estimate <= 1e-7
+    assert i1.iterations > i0.iterations
+    s.close()
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_generic_path_large_d(sld, oracle_mod, precision, monkeypatch):
     """The register-sweep kernel with d = 512 (label sums in global per-warp
