@@ -309,8 +309,8 @@ def bench_spe10(sld, torch, fp64=False):
     and d = 1 for reference) on the deflated-CG path, on an SPE10-shaped
     synthetic field (180x220x85): FP32-inner solves with FP64 refinement to
     1e-9, and with fp64 also plain FP64 solves (capped at 30000 iterations:
-    on this 7.5-decade field they stagnate or break down, and take about a
-    minute of GPU time)."""
+    on this 7.5-decade field they may stagnate or break down, depending on
+    the rounding of E, and take up to a minute of GPU time)."""
     from paper_1510_02148_gb300 import workloads as W
     P = W.spe10_like()
     Kd = torch.from_numpy(P.K.reshape(-1)).cuda()

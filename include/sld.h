@@ -231,7 +231,9 @@ sld_status sld_deflation_info(sld_system s, int* d, int* k_requested, int* k_use
  * solve prints |d_k| / |x_k| and ||r_k|| / ||b|| of its first 16
  * refinement steps to stderr.
  * Errors: SLD_ERR_STATE (no deflation built), SLD_ERR_NOT_CONVERGED (x and
- * res still written), SLD_ERR_BREAKDOWN, SLD_ERR_TIMEOUT, SLD_ERR_CUDA.
+ * res still written), SLD_ERR_BREAKDOWN (with SLD_FP64 and finite scalars x
+ * and res are still written: x = x* + P_2 xhat of the last iterate before
+ * p^T P A p <= 0, the progress made), SLD_ERR_TIMEOUT, SLD_ERR_CUDA.
  */
 sld_status sld_solve(sld_system s, const double* b, const sld_options* o, double* x,
                      sld_result* res);

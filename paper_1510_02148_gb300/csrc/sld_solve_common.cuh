@@ -493,6 +493,7 @@ __device__ void solve_body(const SolveArgs& a, double* acc, double* Yd, T* Y, do
     fs[kEst] = -1.0;
   }
   int its = 0, outer = 0, status = 0;
+  bool fin_ok = false;  // a breakdown with finite scalars (see the inner loop)
   bool converged = false;
   bool failed = false;
   if (team_rank(a.sy) == 0 && threadIdx.x == 0) a.out[kOutStartNs] = (double)global_ns();
@@ -590,6 +591,7 @@ __device__ void solve_body(const SolveArgs& a, double* acc, double* Yd, T* Y, do
       const double delta = gamma - cta_take_y(a, Y, red);
       if (!(delta > 0.0) || !isfinite(delta) || !isfinite(rho)) {
         if (a.fp64) status = SLD_ERR_BREAKDOWN;
+        fin_ok = isfinite(delta) && isfinite(rho);
         break;
       }
       const double alpha = rho / delta;
@@ -608,7 +610,10 @@ __device__ void solve_body(const SolveArgs& a, double* acc, double* Yd, T* Y, do
       rho = rho_new;
       pold ^= 1;
     }
-    if (failed || status) break;
+    // a plain FP64 solve that broke down with finite scalars still takes
+    // its finalisation step: x = x* + P^T xhat keeps the iterations' progress
+    // (xhat is the last consistent iterate); the status stays BREAKDOWN
+    if (failed || (status && !(a.fp64 && fin_ok && outer == 1))) break;
   }
   if (team_rank(a.sy) == 0 && threadIdx.x == 0) {
     a.out[kOutIters] = its;
