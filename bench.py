@@ -232,13 +232,14 @@ def bench_c0(sld, torch, reps=5):
 
 def gmres_bytes(n, m, its, cycles, deflated):
     """Algorithmic bytes of a PDGMRES solve: per Arnoldi step with basis size
-    j+1, apply 68 B (v, V_j, w, faces, diag, 1/diag, label), deflation 52 B
-    (w r/w, faces, diag, label), two dot passes (j+1) 8 + 8 B and two
-    orthogonalisation passes (j+1) 8 + 16 B; per cycle the residual (apply,
-    deflation, copy with norm: 68 + 52 + 16 B); plain GMRES drops the
-    deflation pass and the labels."""
-    per_step = (168 if deflated else 112)
-    per_cycle = (136 if deflated else 80)
+    j+1, apply 68 B (raw v, M^-1 v, V_j, w, faces, diag, label), deflation
+    52 B (w r/w, faces, diag, label), two dot passes (j+1) 8 + 8 B and two
+    orthogonalisation passes (j+1) 8 + 16 B, the second one also reading
+    1/diag and writing M^-1 of the next raw vector (+16 B); per cycle the
+    residual (apply, deflation, copy with norm and M^-1: 68 + 52 + 32 B);
+    plain GMRES drops the deflation pass and the labels."""
+    per_step = (184 if deflated else 128)
+    per_cycle = (152 if deflated else 96)
     tot = 0
     left = its
     for c in range(cycles):

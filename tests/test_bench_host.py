@@ -12,16 +12,18 @@ import bench
 def _tally(n, m, its, deflated):
     """Step by step: a cycle's residual pass, then per Arnoldi step with basis
     size j+1 the apply, the deflation, two dot and two orthogonalisation
-    passes over the basis."""
+    passes over the basis; the pass that writes the next raw vector (the
+    residual copy, the second orthogonalisation) also reads 1/diag and
+    writes M^-1 of it."""
     tot, left = 0, its
     while left > 0:
         k = min(m, left)
         left -= k
-        tot += (68 + 52 + 16) if deflated else (68 + 16 - 4)
+        tot += (68 + 52 + 16 + 16) if deflated else (68 + 16 + 16 - 4)
         for j in range(k):
             dot = (j + 1) * 8 + 8     # basis and w read
             orth = (j + 1) * 8 + 16   # basis read, w read and written
-            step = 68 + 2 * dot + 2 * orth
+            step = 68 + 2 * dot + 2 * orth + 16
             if deflated:
                 step += 52
             else:
