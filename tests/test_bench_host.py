@@ -65,3 +65,43 @@ def test_peaks_from_measured_file():
         assert kind == "measured" and val == float(json.load(open(p))["hbm_gbs"])
     else:
         assert (val, kind) == (6800.0, "fallback")
+
+
+def _fake_smi(tmp_path, body):
+    d = tmp_path / "bin"
+    d.mkdir()
+    f = d / "nvidia-smi"
+    f.write_text("#!/bin/sh\n" + body)
+    f.chmod(0o755)
+    return str(d)
+
+
+def test_clock_sampler_opens_after_the_first_sample(tmp_path, monkeypatch):
+    """The sampler returns from __enter__ once nvidia-smi has printed its
+    first line (its start-up happens before the timed region), and keeps
+    collecting afterwards."""
+    import time
+    line = "0, 2070, 2070, 900.0, 0x0, Not Active, Not Active, Not Active, Not Active"
+    fake = _fake_smi(tmp_path, f"sleep 0.3\nwhile true; do echo '{line}'; sleep 0.05; done\n")
+    monkeypatch.setenv("PATH", fake + os.pathsep + os.environ.get("PATH", ""))
+    t0 = time.perf_counter()
+    with bench.ClockSampler() as c:
+        waited = time.perf_counter() - t0
+        assert c.lines and waited >= 0.25
+        time.sleep(0.2)
+    assert len(c.lines) >= 2 and c.summary()["sm_mhz"] == 2070
+
+
+def test_clock_sampler_without_nvidia_smi(tmp_path, monkeypatch):
+    """No nvidia-smi, or one that exits at once: no wait, an empty record."""
+    import time
+    monkeypatch.setenv("PATH", str(tmp_path))
+    t0 = time.perf_counter()
+    with bench.ClockSampler() as c:
+        pass
+    assert time.perf_counter() - t0 < 2.0 and c.summary()["samples"] == 0
+    monkeypatch.setenv("PATH", _fake_smi(tmp_path, "exit 0\n") + os.pathsep + os.environ.get("PATH", ""))
+    t0 = time.perf_counter()
+    with bench.ClockSampler() as c:
+        pass
+    assert time.perf_counter() - t0 < 2.0 and c.summary()["samples"] == 0
