@@ -105,9 +105,19 @@ sld_status ensure_workspace(sld_system s, bool need_fp32, bool need_bf16) {
       return cuda_fail(e, "alloc y");
   }
   if (need_fp32 && !s->Tx32) {
-    if ((e = dalloc(&s->Tx32, s->np)) != cudaSuccess) return cuda_fail(e, "alloc Tx32");
-    if ((e = dalloc(&s->Ty32, s->np)) != cudaSuccess) return cuda_fail(e, "alloc Ty32");
-    if ((e = dalloc(&s->Tz32, s->np)) != cudaSuccess) return cuda_fail(e, "alloc Tz32");
+    // all three or none, so that a failed allocation leaves no half-made set
+    float *tx = nullptr, *ty = nullptr, *tz = nullptr;
+    if ((e = dalloc(&tx, s->np)) != cudaSuccess || (e = dalloc(&ty, s->np)) != cudaSuccess ||
+        (e = dalloc(&tz, s->np)) != cudaSuccess) {
+      dfree(tx);
+      dfree(ty);
+      dfree(tz);
+      cudaGetLastError();
+      return cuda_fail(e, "alloc FP32 faces");
+    }
+    s->Tx32 = tx;
+    s->Ty32 = ty;
+    s->Tz32 = tz;
     if ((e = sld::launch_quantize_fp32(s)) != cudaSuccess) return cuda_fail(e, "fp32 coefficients");
   }
   if (need_bf16 && !s->bf16_ready) {
@@ -471,8 +481,15 @@ sld_status sld_solve(sld_system s, const double* b, const sld_options* opt, doub
   // modes of this field, so the solve goes on from its x with FP32-inner
   // refinement steps (the FP32 faces are made on first use).
   const double fwd_eff = o.fwd_tol == 0.0 ? 100.0 * o.tol : o.fwd_tol;
-  if (code == SLD_OK && o.precision == SLD_BF16COEF_IR && o.fwd_tol >= 0.0 && r.fwd_err_estimate > fwd_eff) {
-    if ((st = ensure_workspace(s, true, false)) != SLD_OK) return st;
+  bool hand_on = code == SLD_OK && o.precision == SLD_BF16COEF_IR && o.fwd_tol >= 0.0 && r.fwd_err_estimate > fwd_eff;
+  if (hand_on && ensure_workspace(s, true, false) != SLD_OK) {
+    // no room for the FP32 faces: the BF16 result stands (its estimate above
+    // fwd_tol tells the caller)
+    hand_on = false;
+    g_last_error.clear();
+    cudaGetLastError();
+  }
+  if (hand_on) {
     sld_options o2 = o;
     o2.precision = SLD_FP32_IR;
     sld_result r2{};
