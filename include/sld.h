@@ -116,7 +116,8 @@ typedef struct {
                              from its x with SLD_FP32_IR refinement steps (FP32
                              faces made on first use), and sld_result counts
                              both parts (iterations, outer steps, solve_ms; the
-                             estimate is the FP32 part's).
+                             estimate is the FP32 part's).  Without device
+                             memory for the FP32 faces the BF16 result stands.
                              0 = 100 * tol (the default); < 0 = off (the
                              residual test alone: fewer steps on high-contrast
                              fields, larger error along the smallest
